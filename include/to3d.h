@@ -1,0 +1,198 @@
+/*
+ * to3d.h -- C interface of the GB300 SIMP / Optimality Criteria hot path.
+ *
+ * The library solves the compliance-minimisation problem of Kim & Kang,
+ * "PyTopo3D" (arXiv 2504.05604): a structured grid of nelx x nely x nelz unit
+ * 8-node hexahedra (Section 2.2), SIMP moduli E_e = Emin + x_e^p (E0 - Emin)
+ * (Section 2.3), the linear-decay rmin filter (Section 2.4) and the OC update
+ * with bisection on the volume multiplier (Section 2.3), iterated as in
+ * Section 2.5.  Every step runs in the library's own CUDA kernels on one GPU.
+ *
+ * Numbering (all arrays at this interface are unpadded):
+ *   element (i,j,k) -> e = i + nelx*(j + nely*k)              [nel]
+ *   node    (i,j,k) -> n = i + (nelx+1)*(j + (nely+1)*k)      [N]
+ *   dof             -> 3*n + c, c = 0 (x), 1 (y), 2 (z)       [3N]
+ *   element-local node a + 2b + 4c sits at corner (i+a, j+b, k+c).
+ *
+ * Conventions:
+ *   - Status codes only; no exceptions or aborts cross this boundary.
+ *     to3d_last_error() gives a message for the last failure on a context.
+ *   - Inputs to to3d_create are copied; the caller keeps ownership of its
+ *     buffers.  Outputs go to caller-allocated buffers.
+ *   - `on_device` = 1: the pointers are CUDA device pointers (e.g. torch
+ *     tensor data_ptr()) on the context's device; 0: host pointers.  Host
+ *     pointers are copied through the context's stream and the call
+ *     returns after the copy back has completed.
+ *   - All GPU work is enqueued on the stream given at create (NULL = the
+ *     legacy default stream).  A context is used by one host thread at a time.
+ *   - Clamped dofs: the operator is K restricted to the free dofs with unit
+ *     rows/columns on the clamped ones (Section 2.2, "modifying the system
+ *     matrix and load vector"); loads on clamped dofs are ignored.
+ */
+#ifndef TO3D_H
+#define TO3D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TO3D_API __attribute__((visibility("default")))
+#else
+#define TO3D_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TO3D_OK = 0,
+    TO3D_EINVAL = 1,    /* bad argument or size                                */
+    TO3D_ENOMEM = 2,    /* device or host allocation failed                    */
+    TO3D_ECUDA = 3,     /* a CUDA runtime call failed                          */
+    TO3D_ENOCONV = 4,   /* solver reached its iteration limit                  */
+    TO3D_ENUMERIC = 5,  /* NaN/Inf or non-positive curvature in a solver       */
+    TO3D_ETIMEOUT = 6,  /* a bounded device-side wait gave up                  */
+    TO3D_ESTATE = 7     /* call not valid in the context's current state       */
+} to3d_status;
+
+/* Arithmetic of the equilibrium solve.  The *_DC forms run an inner
+ * conjugate-gradient solve with FP32 vectors and a tensor-core element
+ * matvec (integer-exact stiffness, 16-bit displacement operands, FP32
+ * accumulation) inside an FP64 defect-correction loop: r = f - K u in FP64,
+ * FP64 dot products and norms, u += d in FP64. */
+typedef enum {
+    TO3D_F64 = 0,        /* FP64 Jacobi-PCG with the FP64 element matvec      */
+    TO3D_BF16_DC = 1,    /* BF16 operand (one slice)                          */
+    TO3D_BF16X2_DC = 2,  /* BF16 hi + lo slices (about 16 mantissa bits)      */
+    TO3D_FP16_DC = 3     /* FP16 operand with per-element power-of-two scale  */
+} to3d_precision;
+
+typedef enum { TO3D_JACOBI = 0, TO3D_CNN_FCG = 1 } to3d_precond;
+typedef enum { TO3D_FILTER_SENS = 0, TO3D_FILTER_DENS = 1 } to3d_filter;
+
+typedef struct {
+    int32_t nelx, nely, nelz;
+    double volfrac;      /* volume fraction of the design elements            */
+    double penal;        /* SIMP power p                                      */
+    double rmin;         /* filter radius in element lengths                  */
+    double E0, Emin, nu; /* solid modulus, void modulus, Poisson ratio        */
+    double move;         /* OC move limit                                     */
+    double bisect_tol;   /* stop bisection when (l2-l1)/(l1+l2) <= tol        */
+    double cg_rtol;      /* stop when ||f - K u||_2 <= cg_rtol ||f||_2        */
+    double inner_rtol;   /* *_DC forms: inner solve relative tolerance        */
+    int32_t cg_maxit;    /* iteration limit of one solve (all inner steps)    */
+    int32_t filter;      /* to3d_filter                                       */
+    int32_t precision;   /* to3d_precision                                    */
+    int32_t precond;     /* to3d_precond                                      */
+    int32_t oc_levels;   /* bisection levels resolved per reduction pass, 1-6 */
+    int32_t warm_start;  /* 1: start each solve from the previous u           */
+    int32_t reserved[6];
+} to3d_params;
+
+typedef struct {
+    int32_t iter;        /* 0-based OC iteration index                        */
+    int32_t status;      /* to3d_status of the iteration                      */
+    double compliance;   /* c = f^T u = sum_e E_e u_e^T KE u_e                 */
+    double volume;       /* design volume fraction after the update           */
+    double change;       /* max_e |x_new - x|                                 */
+    double lambda;       /* last bisection midpoint                           */
+    double relres;       /* final true relative residual of the solve         */
+    int32_t cg_iters;    /* inner (or plain) CG iterations of the solve       */
+    int32_t outer_iters; /* defect-correction steps (1 for TO3D_F64)          */
+    int32_t halvings;    /* bisection halvings                                */
+    int32_t pad;
+    double ms_solve, ms_sens, ms_filter, ms_oc;   /* CUDA-event phase times   */
+} to3d_iter_info;
+
+typedef struct {
+    int32_t iters, outer, status, pad;
+    double relres;
+} to3d_solve_info;
+
+typedef struct to3d_ctx to3d_ctx;
+
+/* Fill *p with the defaults: E0 = 1, Emin = 1e-9, nu = 0.3, penal = 3,
+ * volfrac = 0.3, rmin = 1.5, move = 0.2, bisect_tol = 1e-3, cg_rtol = 1e-8,
+ * inner_rtol = 1e-4, cg_maxit = 200000, sensitivity filter, TO3D_F64,
+ * Jacobi, oc_levels = 3, warm_start = 1.  Grid sizes are set to 0. */
+TO3D_API to3d_status to3d_default_params(to3d_params* p);
+
+/* Create a context for one problem.
+ *   fixed   [3N] uint8, host: nonzero = clamped dof (Section 2.2).
+ *   load    [3N] double, host: nodal forces F (Section 2.2, K U = F).
+ *   passive [nel] uint8, host, may be NULL: 0 design, 1 void (x pinned at 0),
+ *           2 solid (x pinned at 1); pinned elements are excluded from the
+ *           volume constraint (Section 2.3, passive regions).
+ *   stream  cudaStream_t (as void*) on which all work is enqueued.
+ * The density starts at volfrac on design elements.
+ * Errors: EINVAL for non-positive sizes or parameters out of range, ENOMEM,
+ * ECUDA.  *out is NULL on failure. */
+TO3D_API to3d_status to3d_create(const to3d_params* p, const uint8_t* fixed, const double* load,
+                        const uint8_t* passive, void* stream, to3d_ctx** out);
+
+TO3D_API void to3d_destroy(to3d_ctx* ctx);
+TO3D_API const char* to3d_last_error(const to3d_ctx* ctx);
+TO3D_API const char* to3d_status_string(to3d_status s);
+/* Number of this library's kernel launches issued on the context so far. */
+TO3D_API int64_t to3d_launch_count(const to3d_ctx* ctx);
+
+/* One OC iteration (Section 2.5): solve K(x) u = f, element energies and
+ * sensitivities, filter, OC update of x.  `info` may be NULL. */
+TO3D_API to3d_status to3d_step(to3d_ctx* ctx, to3d_iter_info* info);
+/* `iters` OC iterations; hist [iters] may be NULL. */
+TO3D_API to3d_status to3d_run(to3d_ctx* ctx, int32_t iters, to3d_iter_info* hist);
+
+/* Current design x [nel] (FP64) and last displacement u [3N] (FP64). */
+TO3D_API to3d_status to3d_get_density(to3d_ctx* ctx, double* x, int32_t on_device);
+TO3D_API to3d_status to3d_set_density(to3d_ctx* ctx, const double* x, int32_t on_device);
+TO3D_API to3d_status to3d_get_displacement(to3d_ctx* ctx, double* u, int32_t on_device);
+
+/* ---- single steps of the path (also used by the parity tests) ---------- */
+
+/* y = Kbar(x) p in FP64 (Section 2.2 operator with clamped dofs as identity
+ * rows/columns).  x [nel] densities, p, y [3N].  Matrix-free: K is never
+ * formed. */
+TO3D_API to3d_status to3d_matvec(to3d_ctx* ctx, const double* x, const double* p, double* y,
+                        int32_t on_device);
+
+/* y = Kbar(x) p with the tensor-core element matvec of precision `prec`
+ * (TO3D_BF16_DC, TO3D_BF16X2_DC or TO3D_FP16_DC): p rounded per element to
+ * the 16-bit operand format, integer-exact element stiffness, FP32
+ * accumulation, FP32 scaling by E_e.  p, y [3N] FP32. */
+TO3D_API to3d_status to3d_matvec_lowp(to3d_ctx* ctx, const double* x, const float* p, float* y,
+                             int32_t prec, int32_t on_device);
+
+/* Solve Kbar(x) u = f to ||f - Kbar u|| <= cg_rtol ||f|| with the context's
+ * precision and preconditioner.  f may be NULL (the context's load).
+ * u [3N] is the result (its input value is the initial guess when
+ * warm_start = 1, else ignored). */
+TO3D_API to3d_status to3d_solve(to3d_ctx* ctx, const double* x, const double* f, double* u,
+                       int32_t on_device, to3d_solve_info* info);
+
+/* ce_e = u_e^T KE u_e, dc_e = -p x_e^(p-1) (E0 - Emin) ce_e and
+ * c = sum_e E_e ce_e (Section 2.3).  ce, dc [nel]; *compliance on host. */
+TO3D_API to3d_status to3d_sensitivity(to3d_ctx* ctx, const double* x, const double* u, double* ce,
+                             double* dc, double* compliance, int32_t on_device);
+
+/* Filter (Section 2.4) with H_ei = max(0, rmin - |c_e - c_i|), Hs_e its
+ * in-grid row sum.  Sensitivity filter: out = H(x dc) / (Hs max(1e-3, x));
+ * density filter (TO3D_FILTER_DENS): out = H v / Hs, and its transpose
+ * (chain rule) when `transpose` = 1: out = H^T (v / Hs). */
+TO3D_API to3d_status to3d_filter_apply(to3d_ctx* ctx, int32_t kind, const double* x, const double* v,
+                              double* out, int32_t transpose, int32_t on_device);
+
+/* OC update (Section 2.3) of x with filtered sensitivities dcf:
+ * x_new = clamp(x sqrt(-dcf/lambda), max(0, x - move), min(1, x + move)),
+ * lambda by bisection on [0, 1e9] until (l2-l1)/(l1+l2) <= bisect_tol, the
+ * design volume sum_design x_new > volfrac * n_design raising l1.
+ * Passive elements are pinned.  Outputs on host: lambda, design volume
+ * (absolute), halvings; xnew [nel] as `on_device` says. */
+TO3D_API to3d_status to3d_oc_update(to3d_ctx* ctx, const double* x, const double* dcf, double* xnew,
+                           double* lambda, double* volume, int32_t* halvings,
+                           int32_t on_device);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TO3D_H */

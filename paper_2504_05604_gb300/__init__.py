@@ -1,0 +1,9 @@
+"""GB300-native SIMP + Optimality Criteria hot path (arXiv 2504.05604).
+
+The compute lives in the CUDA library ``libto3d.so`` (sources in ``csrc/``,
+interface in ``include/to3d.h``); ``binding`` is its ctypes binding.
+"""
+from .binding import (  # noqa: F401
+    Context, To3dError, default_params, load, exported_symbols,
+    F64, BF16_DC, BF16X2_DC, FP16_DC, JACOBI, CNN_FCG, FILTER_SENS, FILTER_DENS,
+)

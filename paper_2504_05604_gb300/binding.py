@@ -1,0 +1,288 @@
+"""ctypes binding of the to3d C interface (include/to3d.h).
+
+Argument marshalling only: every step of the path runs in the CUDA library.
+Arrays may be NumPy arrays (host memory, ``on_device = 0``) or CUDA torch
+tensors (device memory, ``on_device = 1``); the work goes on the stream the
+context was created with (by default torch's current stream).
+
+If the library is missing or cannot be loaded the import fails loudly: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libto3d.so")
+
+F64, BF16_DC, BF16X2_DC, FP16_DC = 0, 1, 2, 3
+JACOBI, CNN_FCG = 0, 1
+FILTER_SENS, FILTER_DENS = 0, 1
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error",
+          4: "no convergence", 5: "numerical breakdown", 6: "device wait timed out",
+          7: "invalid state"}
+
+
+class Params(C.Structure):
+    _fields_ = [("nelx", C.c_int32), ("nely", C.c_int32), ("nelz", C.c_int32),
+                ("volfrac", C.c_double), ("penal", C.c_double), ("rmin", C.c_double),
+                ("E0", C.c_double), ("Emin", C.c_double), ("nu", C.c_double),
+                ("move", C.c_double), ("bisect_tol", C.c_double), ("cg_rtol", C.c_double),
+                ("inner_rtol", C.c_double),
+                ("cg_maxit", C.c_int32), ("filter", C.c_int32), ("precision", C.c_int32),
+                ("precond", C.c_int32), ("oc_levels", C.c_int32), ("warm_start", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
+
+
+class IterInfo(C.Structure):
+    _fields_ = [("iter", C.c_int32), ("status", C.c_int32),
+                ("compliance", C.c_double), ("volume", C.c_double), ("change", C.c_double),
+                ("lam", C.c_double), ("relres", C.c_double),
+                ("cg_iters", C.c_int32), ("outer_iters", C.c_int32), ("halvings", C.c_int32),
+                ("pad", C.c_int32),
+                ("ms_solve", C.c_double), ("ms_sens", C.c_double), ("ms_filter", C.c_double),
+                ("ms_oc", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("outer", C.c_int32), ("status", C.c_int32),
+                ("pad", C.c_int32), ("relres", C.c_double)]
+
+
+class To3dError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"to3d status {status} ({STATUS.get(status, '?')}): {msg}")
+        self.status = status
+
+
+_lib = None
+VP, I32, DP = C.c_void_p, C.c_int32, C.POINTER(C.c_double)
+
+_SIGS = {
+    "to3d_default_params": (I32, [C.POINTER(Params)]),
+    "to3d_create": (I32, [C.POINTER(Params), VP, VP, VP, VP, C.POINTER(VP)]),
+    "to3d_destroy": (None, [VP]),
+    "to3d_last_error": (C.c_char_p, [VP]),
+    "to3d_status_string": (C.c_char_p, [I32]),
+    "to3d_launch_count": (C.c_int64, [VP]),
+    "to3d_step": (I32, [VP, C.POINTER(IterInfo)]),
+    "to3d_run": (I32, [VP, I32, C.POINTER(IterInfo)]),
+    "to3d_get_density": (I32, [VP, VP, I32]),
+    "to3d_set_density": (I32, [VP, VP, I32]),
+    "to3d_get_displacement": (I32, [VP, VP, I32]),
+    "to3d_matvec": (I32, [VP, VP, VP, VP, I32]),
+    "to3d_matvec_lowp": (I32, [VP, VP, VP, VP, I32, I32]),
+    "to3d_solve": (I32, [VP, VP, VP, VP, I32, C.POINTER(SolveInfo)]),
+    "to3d_sensitivity": (I32, [VP, VP, VP, VP, VP, DP, I32]),
+    "to3d_filter_apply": (I32, [VP, I32, VP, VP, VP, I32, I32]),
+    "to3d_oc_update": (I32, [VP, VP, VP, VP, DP, DP, C.POINTER(I32), I32]),
+}
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def load(path: str = LIB_PATH):
+    """Load libto3d.so (built by ``build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: build the CUDA library first "
+                          "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load().to3d_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+class _Arg:
+    """Pointer + on_device flag for a NumPy array or a CUDA torch tensor."""
+
+    def __init__(self, a, dtype):
+        if _is_torch(a):
+            import torch
+            want = {np.float64: torch.float64, np.float32: torch.float32,
+                    np.uint8: torch.uint8}[dtype]
+            if not a.is_cuda or a.dtype != want or not a.is_contiguous():
+                raise TypeError(f"expected a contiguous CUDA {want} tensor")
+            self.obj, self.ptr, self.dev = a, a.data_ptr(), 1
+        else:
+            arr = np.ascontiguousarray(a, dtype=dtype)
+            self.obj, self.ptr, self.dev = arr, arr.ctypes.data, 0
+
+
+def _same_kind(*args):
+    devs = {a.dev for a in args if a is not None}
+    if len(devs) > 1:
+        raise TypeError("mix of host and device arrays in one call")
+    return devs.pop() if devs else 0
+
+
+class Context:
+    """One problem on one GPU (wraps ``to3d_create`` / ``to3d_destroy``)."""
+
+    def __init__(self, nelx, nely, nelz, fixed, load_vec, passive=None, stream=None, **params):
+        lib = load()
+        self.lib = lib
+        self.params = default_params(nelx=nelx, nely=nely, nelz=nelz, **params)
+        self.nelx, self.nely, self.nelz = nelx, nely, nelz
+        self.nel = nelx * nely * nelz
+        self.ndof = 3 * (nelx + 1) * (nely + 1) * (nelz + 1)
+        fixed = np.ascontiguousarray(fixed, np.uint8)
+        load_vec = np.ascontiguousarray(load_vec, np.float64)
+        if fixed.size != self.ndof or load_vec.size != self.ndof:
+            raise ValueError("fixed/load must have 3N entries")
+        pas = None
+        if passive is not None:
+            pas = np.ascontiguousarray(passive, np.uint8)
+            if pas.size != self.nel:
+                raise ValueError("passive must have nel entries")
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = 0
+        h = VP()
+        st = lib.to3d_create(C.byref(self.params), fixed.ctypes.data, load_vec.ctypes.data,
+                             pas.ctypes.data if pas is not None else None, VP(stream), C.byref(h))
+        if st != 0:
+            raise To3dError(st, "to3d_create failed")
+        self.h = h
+
+    @classmethod
+    def from_problem(cls, prob, **params):
+        kw = dict(volfrac=prob.volfrac, penal=prob.penal, rmin=prob.rmin, E0=prob.E0,
+                  Emin=prob.Emin, nu=prob.nu, move=prob.move, bisect_tol=prob.bisect_tol)
+        kw.update(params)
+        return cls(prob.nelx, prob.nely, prob.nelz, prob.fixed, prob.load, prob.passive, **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.to3d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != 0:
+            msg = self.lib.to3d_last_error(self.h)
+            raise To3dError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.to3d_launch_count(self.h))
+
+    # ---- whole iterations
+    def step(self) -> dict:
+        info = IterInfo()
+        self._check(self.lib.to3d_step(self.h, C.byref(info)), "to3d_step")
+        return info.as_dict()
+
+    def run(self, iters: int):
+        hist = (IterInfo * max(iters, 1))()
+        self._check(self.lib.to3d_run(self.h, iters, hist), "to3d_run")
+        return [hist[i].as_dict() for i in range(iters)]
+
+    def density(self, out=None):
+        out = np.empty(self.nel) if out is None else out
+        a = _Arg(out, np.float64)
+        self._check(self.lib.to3d_get_density(self.h, a.ptr, a.dev), "get_density")
+        return out
+
+    def set_density(self, x):
+        a = _Arg(x, np.float64)
+        self._check(self.lib.to3d_set_density(self.h, a.ptr, a.dev), "set_density")
+
+    def displacement(self, out=None):
+        out = np.empty(self.ndof) if out is None else out
+        a = _Arg(out, np.float64)
+        self._check(self.lib.to3d_get_displacement(self.h, a.ptr, a.dev), "get_displacement")
+        return out
+
+    # ---- single steps
+    def matvec(self, x, p, y=None):
+        y = np.empty(self.ndof) if y is None else y
+        ax, ap, ay = _Arg(x, np.float64), _Arg(p, np.float64), _Arg(y, np.float64)
+        dev = _same_kind(ax, ap, ay)
+        self._check(self.lib.to3d_matvec(self.h, ax.ptr, ap.ptr, ay.ptr, dev), "matvec")
+        return y
+
+    def matvec_lowp(self, x, p32, prec=BF16_DC, y=None):
+        y = np.empty(self.ndof, np.float32) if y is None else y
+        ax, ap, ay = _Arg(x, np.float64), _Arg(p32, np.float32), _Arg(y, np.float32)
+        dev = _same_kind(ax, ap, ay)
+        self._check(self.lib.to3d_matvec_lowp(self.h, ax.ptr, ap.ptr, ay.ptr, prec, dev),
+                    "matvec_lowp")
+        return y
+
+    def solve(self, x, f=None, u=None):
+        u = np.zeros(self.ndof) if u is None else u
+        ax, au = _Arg(x, np.float64), _Arg(u, np.float64)
+        af = _Arg(f, np.float64) if f is not None else None
+        dev = _same_kind(ax, au, af)
+        info = SolveInfo()
+        st = self.lib.to3d_solve(self.h, ax.ptr, af.ptr if af else None, au.ptr, dev,
+                                 C.byref(info))
+        self._check(st, "solve")
+        return u, {"iters": info.iters, "outer": info.outer, "status": info.status,
+                   "relres": info.relres}
+
+    def sensitivity(self, x, u, ce=None, dc=None):
+        ce = np.empty(self.nel) if ce is None else ce
+        dc = np.empty(self.nel) if dc is None else dc
+        ax, au, ac, ad = (_Arg(x, np.float64), _Arg(u, np.float64), _Arg(ce, np.float64),
+                          _Arg(dc, np.float64))
+        dev = _same_kind(ax, au, ac, ad)
+        comp = C.c_double()
+        self._check(self.lib.to3d_sensitivity(self.h, ax.ptr, au.ptr, ac.ptr, ad.ptr,
+                                              C.byref(comp), dev), "sensitivity")
+        return ce, dc, comp.value
+
+    def filter(self, v, x=None, kind=FILTER_SENS, transpose=False, out=None):
+        out = np.empty(self.nel) if out is None else out
+        av, ao = _Arg(v, np.float64), _Arg(out, np.float64)
+        ax = _Arg(x, np.float64) if x is not None else None
+        dev = _same_kind(av, ao, ax)
+        self._check(self.lib.to3d_filter_apply(self.h, kind, ax.ptr if ax else None, av.ptr,
+                                               ao.ptr, int(transpose), dev), "filter")
+        return out
+
+    def oc_update(self, x, dcf, xnew=None):
+        xnew = np.empty(self.nel) if xnew is None else xnew
+        ax, ad, an = _Arg(x, np.float64), _Arg(dcf, np.float64), _Arg(xnew, np.float64)
+        dev = _same_kind(ax, ad, an)
+        lam, vol, nh = C.c_double(), C.c_double(), I32()
+        self._check(self.lib.to3d_oc_update(self.h, ax.ptr, ad.ptr, an.ptr, C.byref(lam),
+                                            C.byref(vol), C.byref(nh), dev), "oc_update")
+        return xnew, lam.value, vol.value, nh.value

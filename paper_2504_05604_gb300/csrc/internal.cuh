@@ -1,0 +1,172 @@
+// Internal declarations of the to3d CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/to3d.h"
+
+namespace to3d {
+
+// ---------------------------------------------------------------- geometry
+struct Grid {
+    int nelx, nely, nelz;     // elements per axis
+    int nx, ny, nz;           // nodes per axis (= elements + 1)
+    long long nel, nnode;
+};
+
+__host__ __device__ inline long long elem_id(const Grid& g, int i, int j, int k) {
+    return (long long)i + (long long)g.nelx * ((long long)j + (long long)g.nely * k);
+}
+__host__ __device__ inline long long node_id(const Grid& g, int i, int j, int k) {
+    return (long long)i + (long long)g.nx * ((long long)j + (long long)g.ny * k);
+}
+
+// Element stiffness for unit modulus, passed by value to kernels (it lives in
+// the kernel parameter constant bank, so each context may use its own nu).
+struct KE64 { double v[576]; };
+// Integer split KE = c_lam * A_lam + c_mu * A_mu (A_lam, A_mu integer-valued).
+struct KESplit { float a_lam[576]; float a_mu[576]; double c_lam, c_mu; };
+
+// Filter stencil: integer offsets and weights rmin - |d| > 0.
+constexpr int kMaxStencil = 1200;
+struct Stencil {
+    int n;
+    int radius;
+    int off[kMaxStencil];      // packed (di+16) | (dj+16) << 8 | (dk+16) << 16
+    double w[kMaxStencil];
+};
+
+// ---------------------------------------------------------------- scalars
+// Device-resident solver / OC state, so loops need no host round trip.
+struct SolverScalars {
+    double rz, rz_new, pq, rr, alpha, beta;
+    double fnorm2, tol2;
+    double rr_true;
+    int it, done, status, maxit;
+    int restarts, pad0, pad1, pad2;
+};
+
+struct OCScalars {
+    double l1, l2, lmid, tol, target;
+    double cand[64];          // candidate lambdas of the current pass (tree order)
+    int ncand, levels, halvings, done;
+    int status, maxhalv, pad0, pad1;
+    double volume, change;
+};
+
+// Grid-wide deterministic reductions: per-block partials, last block sums.
+struct Reducer {
+    double* partials = nullptr;   // [kMaxReduceVals][kMaxBlocks]
+    unsigned int* counter = nullptr;
+};
+constexpr int kMaxReduceVals = 64;
+constexpr int kMaxBlocks = 1 << 16;
+
+const char* status_name(to3d_status s);
+
+}  // namespace to3d
+
+// ---------------------------------------------------------------- context
+struct to3d_ctx {
+    to3d_params prm;
+    to3d::Grid g;
+    cudaStream_t stream = nullptr;        // caller's stream
+    cudaStream_t cap_stream = nullptr;    // private stream used only for graph capture
+    int device = 0;
+    std::string err;
+    long long launches = 0;
+    int iter = 0;
+    bool have_u = false;
+    bool have_dinv = false;
+
+    to3d::KE64 ke;                        // unit-modulus element stiffness
+    to3d::KESplit kes;
+    to3d::Stencil* st = nullptr;          // host copy of the filter stencil
+
+    // design / element arrays [nel]
+    double *x = nullptr, *xnew = nullptr, *E = nullptr;
+    float* E32 = nullptr;
+    double *ce = nullptr, *dc = nullptr, *dcf = nullptr, *Hs = nullptr;
+    double *ocq = nullptr, *oclo = nullptr, *ochi = nullptr;
+    uint8_t* passive = nullptr;
+    // node arrays
+    uint8_t* nodemask = nullptr;          // [N] bit c set = dof c clamped
+    double* dinv = nullptr;               // [N] 1/diag (same for the 3 dofs), 0 if all clamped
+    float* dinv32 = nullptr;
+    // dof arrays [3N]
+    double *f = nullptr, *ftmp = nullptr, *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr,
+           *tmp = nullptr;
+    float *d32 = nullptr, *r32 = nullptr, *p32a = nullptr, *p32b = nullptr, *q32 = nullptr;
+    // scratch for API calls with host pointers
+    void* stage = nullptr;
+    size_t stage_bytes = 0, stage_slot = 0;
+    int* dev_err = nullptr;               // device error word of the tensor-core kernels
+    long long ndesign = 0;                // number of design (non-passive) elements
+
+    to3d::Reducer red;
+    to3d::SolverScalars* ss = nullptr;    // device
+    to3d::SolverScalars* ss_h = nullptr;  // pinned host mirror
+    to3d::OCScalars* os = nullptr;
+    to3d::OCScalars* os_h = nullptr;
+    double* misc = nullptr;               // device scalars: [0] compliance, [1] volume, [2] change
+    double* misc_h = nullptr;
+    double fnorm = 0.0;
+
+    cudaEvent_t ev[8] = {};
+    cudaGraphExec_t g_pcg64 = nullptr;    // chunk of FP64 PCG iterations
+    cudaGraphExec_t g_pcg32 = nullptr;    // chunk of inner FP32 PCG iterations
+    int g_pcg32_prec = -1;
+    int chunk = 32;
+};
+
+// ---------------------------------------------------------------- launchers
+namespace to3d {
+
+// error helpers (api.cu)
+to3d_status set_err(to3d_ctx* c, to3d_status s, const std::string& msg);
+to3d_status cuda_check(to3d_ctx* c, cudaError_t e, const char* what);
+to3d_status launch_check(to3d_ctx* c, const char* what);
+
+// matvec64.cu
+void launch_matvec64(to3d_ctx* c, cudaStream_t s, const double* E, const double* p, double* y,
+                     bool dot_pq);
+void launch_diag(to3d_ctx* c, cudaStream_t s, const double* E);
+void launch_simp(to3d_ctx* c, cudaStream_t s, const double* x);
+void launch_residual64(to3d_ctx* c, cudaStream_t s, const double* f, const double* Ku, double* r,
+                       bool to_ss);
+
+// pcg.cu
+void launch_pcg64_init(to3d_ctx* c, cudaStream_t s);
+void launch_pcg64_iter(to3d_ctx* c, cudaStream_t s);
+void launch_pcg32_init(to3d_ctx* c, cudaStream_t s, const double* r64, double scale);
+void launch_pcg32_iter(to3d_ctx* c, cudaStream_t s, int prec, int parity);
+void launch_axpy_d32(to3d_ctx* c, cudaStream_t s, double inv_scale);
+void launch_norm2(to3d_ctx* c, cudaStream_t s, const double* v, long long n, double* out);
+void launch_ss_reset(to3d_ctx* c, cudaStream_t s, double tol2, int maxit);
+inline void launch_fill_zero(to3d_ctx*, cudaStream_t s, void* ptr, size_t bytes) {
+    cudaMemsetAsync(ptr, 0, bytes, s);
+}
+void launch_mask_copy(to3d_ctx* c, cudaStream_t s, const double* src, double* dst);
+
+// matvec_tc.cu
+void launch_matvec_tc(to3d_ctx* c, cudaStream_t s, const float* E32, const float* p_old,
+                      const float* r, const float* dinv, float* p_new, float* q, int prec,
+                      bool fused_dir);
+void init_tc_attributes();
+
+// element.cu
+void launch_sensitivity(to3d_ctx* c, cudaStream_t s, const double* x, const double* u,
+                        double* ce, double* dc);
+void launch_hs(to3d_ctx* c, cudaStream_t s);
+void launch_filter(to3d_ctx* c, cudaStream_t s, int mode, const double* a, const double* b,
+                   double* out);
+void launch_oc_begin(to3d_ctx* c, cudaStream_t s, const double* x, const double* dcf,
+                     double target);
+void launch_oc_passes(to3d_ctx* c, cudaStream_t s, int npass);
+void launch_oc_apply(to3d_ctx* c, cudaStream_t s, const double* x, double* xnew);
+
+}  // namespace to3d

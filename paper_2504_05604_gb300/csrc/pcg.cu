@@ -1,0 +1,286 @@
+// Jacobi-preconditioned conjugate gradients on the device.
+//
+// The paper solves K U = F directly (Section 2.2).  Here the solve is the
+// textbook PCG with M = diag(K); all scalars (rz, pq, alpha, beta, the
+// convergence flag) live in device memory and are produced by the last
+// block of each reduction, so a run of iterations needs no host round trip
+// and can be captured once as a CUDA graph.  Kernels return at once when the
+// device flag says the solve is finished.
+//
+// FP64 form: matvec64 (q = K p, p.q, alpha) -> update (u, r, rz, |r|^2,
+// beta, flag) -> direction (p = M^-1 r + beta p).
+// Inner FP32 form of the defect-correction solve: the tensor-core matvec
+// fuses the direction update (p_new = M^-1 r + beta p_old, ping-pong
+// buffers) with q = K p_new and p_new.q; the update kernel then does
+// d += alpha p_new, r -= alpha q and the two dot products.  Vectors are FP32;
+// per-thread partial sums of positive terms are FP32, block and grid sums
+// FP64.
+#include "internal.cuh"
+#include "reduce.cuh"
+
+namespace to3d {
+
+constexpr int PCG_THREADS = 256;
+
+__device__ __forceinline__ long long gstride() { return (long long)gridDim.x * blockDim.x; }
+__device__ __forceinline__ long long gtid() {
+    return blockIdx.x * (long long)blockDim.x + threadIdx.x;
+}
+
+__global__ void k_ss_reset(SolverScalars* ss, double tol2, int maxit) {
+    ss->rz = ss->rz_new = ss->pq = ss->rr = ss->alpha = ss->beta = 0.0;
+    ss->tol2 = tol2;
+    ss->it = 0;
+    ss->done = 0;
+    ss->status = 0;
+    ss->maxit = maxit;
+}
+
+// ---------------------------------------------------------------- FP64 form
+// z = M^-1 r, p = z, rz = r.z, rr = r.r
+__global__ void k_pcg64_init(long long nnode, const double* __restrict__ r,
+                             const double* __restrict__ dinv, double* __restrict__ p,
+                             const Reducer red, SolverScalars* ss) {
+    __shared__ double sh[64];
+    __shared__ double out[2];
+    double rz = 0.0, rr = 0.0;
+    for (long long n = gtid(); n < nnode; n += gstride()) {
+        const double di = dinv[n];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double rv = r[3 * n + c];
+            p[3 * n + c] = di * rv;
+            rz += di * rv * rv;
+            rr += rv * rv;
+        }
+    }
+    double v[2] = {rz, rr};
+    if (grid_sum<2>(red, v, sh, out) && threadIdx.x == 0) {
+        ss->rz = out[0];
+        ss->rr = out[1];
+        if (!isfinite(out[0]) || !isfinite(out[1])) {
+            ss->status = TO3D_ENUMERIC;
+            ss->done = 1;
+        } else if (out[1] <= ss->tol2) {
+            ss->done = 1;
+        }
+    }
+}
+
+// u += alpha p, r -= alpha q, rz_new = r.M^-1 r, rr = r.r, beta, flags
+__global__ void k_pcg64_update(long long nnode, double* __restrict__ u, double* __restrict__ r,
+                               const double* __restrict__ p, const double* __restrict__ q,
+                               const double* __restrict__ dinv, const Reducer red,
+                               SolverScalars* ss) {
+    if (ss->done) return;
+    __shared__ double sh[64];
+    __shared__ double out[2];
+    const double alpha = ss->alpha;
+    double rz = 0.0, rr = 0.0;
+    for (long long n = gtid(); n < nnode; n += gstride()) {
+        const double di = dinv[n];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long d = 3 * n + c;
+            u[d] = fma(alpha, p[d], u[d]);
+            const double rv = fma(-alpha, q[d], r[d]);
+            r[d] = rv;
+            rz += di * rv * rv;
+            rr += rv * rv;
+        }
+    }
+    double v[2] = {rz, rr};
+    if (grid_sum<2>(red, v, sh, out) && threadIdx.x == 0) {
+        const double rzn = out[0];
+        ss->beta = rzn / ss->rz;
+        ss->rz = rzn;
+        ss->rr = out[1];
+        ss->it += 1;
+        if (!isfinite(rzn) || !isfinite(out[1])) {
+            ss->status = TO3D_ENUMERIC;
+            ss->done = 1;
+        } else if (out[1] <= ss->tol2) {
+            ss->done = 1;
+        } else if (ss->it >= ss->maxit) {
+            ss->status = TO3D_ENOCONV;
+            ss->done = 1;
+        }
+    }
+}
+
+// p = M^-1 r + beta p
+__global__ void k_pcg64_dir(long long nnode, const double* __restrict__ r,
+                            const double* __restrict__ dinv, double* __restrict__ p,
+                            const SolverScalars* ss) {
+    if (ss->done) return;
+    const double beta = ss->beta;
+    for (long long n = gtid(); n < nnode; n += gstride()) {
+        const double di = dinv[n];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long d = 3 * n + c;
+            p[d] = fma(di, r[d], beta * p[d]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- FP32 inner form
+// r32 = r64 * s (s = 1/||r64||_inf-ish scale chosen by the host: here s = 1 /
+// sqrt(rr/ndof), stored in ss->beta before init), d = 0, p_old = 0, beta = 0.
+// The first fused matvec then builds p = M^-1 r.  rz and rr of the scaled r.
+__global__ void k_pcg32_init(long long nnode, const double* __restrict__ r64, double scale,
+                             const float* __restrict__ dinv, float* __restrict__ r32,
+                             float* __restrict__ d32, float* __restrict__ p_old,
+                             const Reducer red, SolverScalars* ss) {
+    __shared__ double sh[64];
+    __shared__ double out[2];
+    float rz = 0.f, rr = 0.f;
+    double rzd = 0.0, rrd = 0.0;
+    int cnt = 0;
+    for (long long n = gtid(); n < nnode; n += gstride()) {
+        const float di = dinv[n];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long d = 3 * n + c;
+            const float rv = (float)(r64[d] * scale);
+            r32[d] = rv;
+            d32[d] = 0.f;
+            p_old[d] = 0.f;
+            rz = fmaf(di * rv, rv, rz);
+            rr = fmaf(rv, rv, rr);
+        }
+        if (++cnt == 16) { rzd += rz; rrd += rr; rz = rr = 0.f; cnt = 0; }
+    }
+    rzd += rz;
+    rrd += rr;
+    double v[2] = {rzd, rrd};
+    if (grid_sum<2>(red, v, sh, out) && threadIdx.x == 0) {
+        ss->rz = out[0];
+        ss->rr = out[1];
+        ss->beta = 0.0;
+        if (!isfinite(out[0]) || !isfinite(out[1])) {
+            ss->status = TO3D_ENUMERIC;
+            ss->done = 1;
+        } else if (out[1] <= ss->tol2) {
+            ss->done = 1;
+        }
+    }
+}
+
+// d += alpha p, r -= alpha q, rz_new, rr, beta, flags
+__global__ void k_pcg32_update(long long nnode, float* __restrict__ d32, float* __restrict__ r32,
+                               const float* __restrict__ p, const float* __restrict__ q,
+                               const float* __restrict__ dinv, const Reducer red,
+                               SolverScalars* ss) {
+    if (ss->done) return;
+    __shared__ double sh[64];
+    __shared__ double out[2];
+    const float alpha = (float)ss->alpha;
+    float rz = 0.f, rr = 0.f;
+    double rzd = 0.0, rrd = 0.0;
+    int cnt = 0;
+    for (long long n = gtid(); n < nnode; n += gstride()) {
+        const float di = dinv[n];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long d = 3 * n + c;
+            d32[d] = fmaf(alpha, p[d], d32[d]);
+            const float rv = fmaf(-alpha, q[d], r32[d]);
+            r32[d] = rv;
+            rz = fmaf(di * rv, rv, rz);
+            rr = fmaf(rv, rv, rr);
+        }
+        if (++cnt == 16) { rzd += rz; rrd += rr; rz = rr = 0.f; cnt = 0; }
+    }
+    rzd += rz;
+    rrd += rr;
+    double v[2] = {rzd, rrd};
+    if (grid_sum<2>(red, v, sh, out) && threadIdx.x == 0) {
+        const double rzn = out[0];
+        ss->beta = rzn / ss->rz;
+        ss->rz = rzn;
+        ss->rr = out[1];
+        ss->it += 1;
+        if (!isfinite(rzn) || !isfinite(out[1])) {
+            ss->status = TO3D_ENUMERIC;
+            ss->done = 1;
+        } else if (out[1] <= ss->tol2) {
+            ss->done = 1;
+        } else if (ss->it >= ss->maxit) {
+            ss->status = TO3D_ENOCONV;
+            ss->done = 1;
+        }
+    }
+}
+
+// u64 += d32 / scale (FP64 accumulation of the correction)
+__global__ void k_axpy_d32(long long ndof, double* __restrict__ u, const float* __restrict__ d32,
+                           double inv_scale) {
+    for (long long d = gtid(); d < ndof; d += gstride()) u[d] = fma((double)d32[d], inv_scale, u[d]);
+}
+
+__global__ void k_norm2(long long n, const double* __restrict__ v, const Reducer red,
+                        double* out_dev) {
+    __shared__ double sh[32];
+    __shared__ double out[1];
+    double acc = 0.0;
+    for (long long i = gtid(); i < n; i += gstride()) acc += v[i] * v[i];
+    double a[1] = {acc};
+    if (grid_sum<1>(red, a, sh, out) && threadIdx.x == 0) *out_dev = out[0];
+}
+
+static unsigned vec_blocks(long long n) {
+    long long nb = (n + PCG_THREADS - 1) / PCG_THREADS;
+    if (nb > 152 * 8) nb = 152 * 8;
+    if (nb < 1) nb = 1;
+    return (unsigned)nb;
+}
+
+void launch_pcg64_init(to3d_ctx* c, cudaStream_t s) {
+    k_pcg64_init<<<vec_blocks(c->g.nnode), PCG_THREADS, 0, s>>>(c->g.nnode, c->r, c->dinv, c->p,
+                                                                 c->red, c->ss);
+    c->launches++;
+}
+
+void launch_pcg64_iter(to3d_ctx* c, cudaStream_t s) {
+    launch_matvec64(c, s, c->E, c->p, c->q, true);
+    k_pcg64_update<<<vec_blocks(c->g.nnode), PCG_THREADS, 0, s>>>(c->g.nnode, c->u, c->r, c->p,
+                                                                   c->q, c->dinv, c->red, c->ss);
+    k_pcg64_dir<<<vec_blocks(c->g.nnode), PCG_THREADS, 0, s>>>(c->g.nnode, c->r, c->dinv, c->p,
+                                                                c->ss);
+    c->launches += 2;
+}
+
+void launch_pcg32_init(to3d_ctx* c, cudaStream_t s, const double* r64, double scale) {
+    k_pcg32_init<<<vec_blocks(c->g.nnode), PCG_THREADS, 0, s>>>(
+        c->g.nnode, r64, scale, c->dinv32, c->r32, c->d32, c->p32b, c->red, c->ss);
+    c->launches++;
+}
+
+// parity 0: p_old = p32b -> p_new = p32a; parity 1: the reverse.
+void launch_pcg32_iter(to3d_ctx* c, cudaStream_t s, int prec, int parity) {
+    float* p_old = parity ? c->p32a : c->p32b;
+    float* p_new = parity ? c->p32b : c->p32a;
+    launch_matvec_tc(c, s, c->E32, p_old, c->r32, c->dinv32, p_new, c->q32, prec, true);
+    k_pcg32_update<<<vec_blocks(c->g.nnode), PCG_THREADS, 0, s>>>(
+        c->g.nnode, c->d32, c->r32, p_new, c->q32, c->dinv32, c->red, c->ss);
+    c->launches++;
+}
+
+void launch_axpy_d32(to3d_ctx* c, cudaStream_t s, double inv_scale) {
+    const long long ndof = 3 * c->g.nnode;
+    k_axpy_d32<<<vec_blocks(ndof), PCG_THREADS, 0, s>>>(ndof, c->u, c->d32, inv_scale);
+    c->launches++;
+}
+
+void launch_norm2(to3d_ctx* c, cudaStream_t s, const double* v, long long n, double* out) {
+    k_norm2<<<vec_blocks(n), PCG_THREADS, 0, s>>>(n, v, c->red, out);
+    c->launches++;
+}
+
+void launch_ss_reset(to3d_ctx* c, cudaStream_t s, double tol2, int maxit) {
+    k_ss_reset<<<1, 1, 0, s>>>(c->ss, tol2, maxit);
+    c->launches++;
+}
+
+}  // namespace to3d
