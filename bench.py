@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""OC iterations per second of the SIMP + OC hot path on a 480x160x80 cantilever.
+
+One step = one OC iteration of the whole path (SIMP moduli and Jacobi
+diagonal, equilibrium solve to ||f - K u|| <= 1e-8 ||f||, element energies and
+sensitivities, rmin filter, OC bisection update) on the synthetic cantilever
+480x160x80 (load at the centre of the x = nelx face, volfrac 0.2, rmin 2.5).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P]
+  python bench.py --impl reference ...    (the CPU FP64 oracle, bounded sample)
+
+Prints one JSON line (rank 0).  N > 1 (torchrun): independent replicas, one
+per GPU, with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "OC iters/s at 480x160x80, chosen vs plain FP64 Jacobi-PCG at rel.res 1e-8"
+UNIT = "OC iters/s"
+PREC_NAMES = {0: "fp64", 1: "bf16-dc", 2: "bf16x2-dc", 3: "fp16-dc"}
+# Jacobi-PCG iterations per OC iteration used to turn the oracle's measured
+# per-iteration cost into OC iterations/s when no GPU run in the same process
+# supplies the count (reference arm): the mean CG iteration count of OC
+# iterations 4-13 at 480x160x80 measured on GB300 with this library.
+REF_ITERS_PER_OC = 3000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", type=int, default=2, help="0 fp64, 1 bf16, 2 bf16x2, 3 fp16")
+    ap.add_argument("--size", default="480x160x80")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison step")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-leg", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-its", type=float, default=REF_ITERS_PER_OC, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-reps", type=int, default=1, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def dims(args):
+    a, b, c = (int(v) for v in args.size.split("x"))
+    return a, b, c
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def cpu_leg(args):
+    """Time the CPU oracle on a bounded sample of the workload and
+    extrapolate to OC iterations/s (prints one JSON dict)."""
+    import numpy as np
+    from oracle import fem, filters, oc
+    from synth import problems
+
+    nelx, nely, nelz = dims(args)
+    KE = fem.element_stiffness(0.3)
+    # Jacobi-PCG iteration cost on a quarter-depth slab of the grid (maxit=2
+    # minus maxit=1; each call also forms the initial and final residuals),
+    # scaled to the full grid by element count
+    zp = max(1, nelz // 4)
+    sp = problems.config_large(nelx=nelx, nely=nely, nelz=zp)
+    x = sp.initial_density()
+    E = fem.simp_modulus(x, sp.penal)
+    f = fem.masked_load(sp.load, sp.fixed)
+    diag = fem.jacobi_diagonal(nelx, nely, zp, E, KE, sp.fixed)
+
+    def mv(v):
+        return fem.matvec_elementwise(nelx, nely, zp, E, KE, v, sp.fixed)
+
+    t = []
+    for m in (1, 2):
+        t0 = time.perf_counter()
+        fem.jacobi_pcg(mv, diag, f, rtol=0.0, maxit=m, true_residual=False)
+        t.append(time.perf_counter() - t0)
+    t_it = max(t[1] - t[0], 1e-9) * (nelz / zp)
+    # once-per-OC-iteration steps on an eighth-depth slab, scaled likewise
+    sz = max(1, nelz // 8)
+    sub = problems.config_large(nelx=nelx, nely=nely, nelz=sz)
+    xs = sub.initial_density()
+    us = problems.random_vector(sub.ndof, 1, 1e-3)
+    t0 = time.perf_counter()
+    ce = fem.element_energies(nelx, nely, sz, KE, us)
+    c, dc = fem.compliance_and_sensitivity(xs, ce, sub.penal)
+    dcf = filters.sensitivity_filter_stencil(nelx, nely, sz, sub.rmin, xs, dc)
+    oc.oc_update(xs, dcf, sub.volfrac, None, sub.move, sub.bisect_tol)
+    t_el = (time.perf_counter() - t0) * (nelz / sz)
+    t_oc = args.cpu_its * t_it + t_el
+    cores = 1
+    return {"value": 1.0 / t_oc, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"oracle (NumPy/SciPy FP64, single-threaded BLAS) on {nelx}x{nely}x{nelz}: "
+                       f"one Jacobi-PCG iteration timed on a {nelx}x{nely}x{zp} slab and scaled by "
+                       f"element count ({t_it:.2f} s), energies+"
+                       f"filter+OC timed on a {nelx}x{nely}x{sz} slab and scaled by element count "
+                       f"({t_el:.2f} s); OC iteration = {args.cpu_its:.0f} PCG iterations + those"),
+            "t_pcg_iter_s": t_it, "t_elementwise_s": t_el, "pcg_iters_per_oc": args.cpu_its}
+
+
+def run_cpu_leg_subprocess(args, its):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-leg", "--size", args.size,
+           "--cpu-its", str(its)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"error": r.stderr[-400:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args):
+    """The oracle as the reference arm: each step is one bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = run_cpu_leg_subprocess(args, args.cpu_its)
+        if "error" in r:
+            print(json.dumps({"impl": "reference", "unavailable": r["error"][-200:]}))
+            return
+        if i >= args.warmup:
+            vals.append(r["value"])
+    v = statistics.mean(vals)
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"cantilever {args.size}, centre load, volfrac 0.2, rmin 2.5",
+                       "sample": "bounded (see cpu_baseline)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ GPU arm
+def algorithmic_bytes_tc(nelx, nely, nelz):
+    """Per launch of the fused tensor-core matvec + direction kernel:
+    read r, p_old (4 B/dof each), M^-1 (4 B/node), E (4 B/element); write
+    p_new and q (4 B/dof each)."""
+    N = (nelx + 1) * (nely + 1) * (nelz + 1)
+    nel = nelx * nely * nelz
+    n = 3 * N
+    return 4 * n * 4 + 4 * N + 4 * nel
+
+
+def ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2504_05604_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2504_05604_gb300 import Context
+    from synth import problems
+
+    nelx, nely, nelz = dims(args)
+    prob = problems.config_large(nelx=nelx, nely=nely, nelz=nelz)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = Context.from_problem(prob, precision=args.precision, stream=stream.cuda_stream)
+    warm = [ctx.step() for _ in range(args.warmup)]
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        ctx.kernel_stats(0, reset=True)
+        ctx.kernel_stats(1, reset=True)
+        l0 = ctx.launches
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clk = ClockSampler(local)
+        barrier()
+        torch.cuda.synchronize()
+        clk.start()
+        ev0.record(stream)
+        recs = [ctx.step() for _ in range(args.steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        launches = ctx.launches - l0
+        tc_ms, tc_n = ctx.kernel_stats(0)
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    value = world * args.steps / (ms / 1000.0)
+    status = max(r["status"] for r in recs)
+    its = [r["cg_iters"] + r["outer_iters"] for r in recs]
+
+    # end to end through the public API with host buffers: per step the
+    # design goes host -> device, one OC iteration runs, the new design and
+    # the iteration record come back
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.empty(prob.nel, dtype=torch.float64).pin_memory().numpy()
+        ctx.density(xh)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.set_density(xh)
+            ctx.step()
+            ctx.density(xh)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        e2e = {"value": world * args.steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": 8 * prob.nel,
+               "d2h_bytes_per_step": 8 * prob.nel + 112}
+
+    # plain FP64 Jacobi-PCG from the same design, one OC iteration
+    fp64 = None
+    if not args.no_fp64 and args.precision != 0:
+        ctx64 = Context.from_problem(prob, precision=0, stream=stream.cuda_stream)
+        xcur = ctx.density()
+        ctx64.set_density(xcur)
+        torch.cuda.synchronize()
+        ctx64.kernel_stats(1, reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r64 = ctx64.step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        m64 = e0.elapsed_time(e1)
+        mv_ms, mv_n = ctx64.kernel_stats(1)
+        fp64 = {"value": 1000.0 / m64, "unit": UNIT, "cg_iters": r64["cg_iters"],
+                "relres": r64["relres"], "matvec_ms": mv_ms / max(mv_n, 1),
+                "oc_iter": r64["iter"], "from_design_after_iter": ctx.params.nelx and recs[-1]["iter"]}
+        ctx64.close()
+
+    if rank != 0:
+        return
+    import json as _json
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = _json.load(fh)
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    tc_avg_ms = tc_ms / tc_n if tc_n else None
+    roof = None
+    if tc_avg_ms:
+        b = algorithmic_bytes_tc(nelx, nely, nelz)
+        ach = b / (tc_avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "kernel": "k_matvec_tc (fused direction + tensor-core K p)",
+                "launch_ms": tc_avg_ms, "algorithmic_bytes": b, "samples": tc_n,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
+    cpu = None
+    if not args.no_cpu and world == 1:
+        cpu = run_cpu_leg_subprocess(args, statistics.mean(its))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 operands, f32 inner CG, f64 defect correction" if args.precision else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"cantilever {args.size}, centre load on x=nelx face, volfrac 0.2, "
+                               f"rmin 2.5, penal 3, OC iterations {args.warmup + 1}-"
+                               f"{args.warmup + args.steps} from x0 = volfrac",
+                   "form": PREC_NAMES[args.precision], "solver_rtol": 1e-8,
+                   "l2": "working set (>1 GB) larger than L2; no flush needed",
+                   "parallelism": f"replicas x{world}"},
+        "gpu_launches": int(launches),
+        "status": int(status),
+        "cg_iters_per_step": its,
+        "phase_ms": {k: statistics.mean(r[k] for r in recs)
+                     for k in ("ms_solve", "ms_sens", "ms_filter", "ms_oc")},
+        "compliance": [r["compliance"] for r in recs],
+        "clocks": clocks,
+        "roofline": roof,
+        "plain_fp64": fp64,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.cpu_leg:
+        print(json.dumps(cpu_leg(args)))
+        return
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    ours(args)
+
+
+if __name__ == "__main__":
+    main()

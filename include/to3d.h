@@ -137,6 +137,14 @@ TO3D_API const char* to3d_status_string(to3d_status s);
 /* Number of this library's kernel launches issued on the context so far. */
 TO3D_API int64_t to3d_launch_count(const to3d_ctx* ctx);
 
+/* Sampled device durations of the solver's dominant kernel launches, taken
+ * with CUDA events recorded inside the captured solver chunks (one launch in
+ * four, launches that did work only).  which = 0: tensor-core matvec of the
+ * defect-correction forms; 1: FP64 matvec.  *ms_total = summed duration,
+ * *samples = number of launches timed; reset = 1 clears the counters. */
+TO3D_API to3d_status to3d_kernel_stats(to3d_ctx* ctx, int32_t which, double* ms_total,
+                                       int64_t* samples, int32_t reset);
+
 /* One OC iteration (Section 2.5): solve K(x) u = f, element energies and
  * sensitivities, filter, OC update of x.  `info` may be NULL. */
 TO3D_API to3d_status to3d_step(to3d_ctx* ctx, to3d_iter_info* info);

@@ -72,6 +72,7 @@ _SIGS = {
     "to3d_last_error": (C.c_char_p, [VP]),
     "to3d_status_string": (C.c_char_p, [I32]),
     "to3d_launch_count": (C.c_int64, [VP]),
+    "to3d_kernel_stats": (I32, [VP, I32, DP, C.POINTER(C.c_int64), I32]),
     "to3d_step": (I32, [VP, C.POINTER(IterInfo)]),
     "to3d_run": (I32, [VP, I32, C.POINTER(IterInfo)]),
     "to3d_get_density": (I32, [VP, VP, I32]),
@@ -202,6 +203,14 @@ class Context:
     @property
     def launches(self) -> int:
         return int(self.lib.to3d_launch_count(self.h))
+
+    def kernel_stats(self, which: int, reset: bool = False):
+        """(summed ms, samples) of sampled launches of the tensor-core (0) or
+        FP64 (1) matvec inside the solver."""
+        ms, n = C.c_double(), C.c_int64()
+        self._check(self.lib.to3d_kernel_stats(self.h, which, C.byref(ms), C.byref(n),
+                                               int(reset)), "kernel_stats")
+        return ms.value, n.value
 
     # ---- whole iterations
     def step(self) -> dict:

@@ -141,7 +141,7 @@ static void free_all(to3d_ctx* c) {
                     c->ochi, c->passive, c->nodemask, c->dinv, c->dinv32, c->f, c->ftmp, c->u,
                     c->r, c->p, c->q, c->tmp, c->d32, c->r32, c->p32a, c->p32b, c->q32,
                     c->stage, c->red.partials, c->red.counter, c->ss, c->os, c->misc,
-                    c->dev_err};
+                    c->dev_err, c->tcB, c->maskp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->ss_h) cudaFreeHost(c->ss_h);
@@ -149,6 +149,9 @@ static void free_all(to3d_ctx* c) {
     if (c->misc_h) cudaFreeHost(c->misc_h);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    for (auto& row : c->kev)
+        for (auto& e : row)
+            if (e) cudaEventDestroy(e);
     if (c->g_pcg64) cudaGraphExecDestroy(c->g_pcg64);
     if (c->g_pcg32) cudaGraphExecDestroy(c->g_pcg32);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -190,6 +193,24 @@ static to3d_status sync_scalars(to3d_ctx* c) {
 }
 
 // ------------------------------------------------------------------ solvers
+static constexpr int kSampleEvery = 4;
+
+// After a captured chunk that started at solver iteration it0 has completed,
+// add the sampled matvec durations of the iterations that did work.
+static void accumulate_kernel_times(to3d_ctx* c, int which, int it0, int it1) {
+    for (int sl = 0; sl < c->kslots[which]; ++sl) {
+        if (it0 + c->kslot_iter[which][sl] >= it1) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->kev[which][2 * sl], c->kev[which][2 * sl + 1]) ==
+            cudaSuccess) {
+            c->kt_ms[which] += ms;
+            c->kt_n[which] += 1;
+        }
+    }
+    cudaGetLastError();
+}
+
+// ------------------------------------------------------------------
 // Launch `n` iterations of the FP64 PCG, through a captured graph when the
 // chunk matches the captured length.
 static to3d_status pcg64_chunk(to3d_ctx* c, int n) {
@@ -197,7 +218,17 @@ static to3d_status pcg64_chunk(to3d_ctx* c, int n) {
         if (!c->g_pcg64) {
             cudaGraph_t gr;
             CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-            for (int i = 0; i < n; ++i) launch_pcg64_iter(c, c->cap_stream);
+            c->kslots[1] = 0;
+            for (int i = 0; i < n; ++i) {
+                cudaEvent_t e0 = nullptr, e1 = nullptr;
+                if (i % kSampleEvery == 0 && c->kslots[1] < to3d_ctx::kTimedSlots) {
+                    const int sl = c->kslots[1]++;
+                    e0 = c->kev[1][2 * sl];
+                    e1 = c->kev[1][2 * sl + 1];
+                    c->kslot_iter[1][sl] = i;
+                }
+                launch_pcg64_iter(c, c->cap_stream, e0, e1);
+            }
             CK(cudaStreamEndCapture(c->cap_stream, &gr));
             CK(cudaGraphInstantiate(&c->g_pcg64, gr, 0));
             cudaGraphDestroy(gr);
@@ -220,7 +251,17 @@ static to3d_status pcg32_chunk(to3d_ctx* c, int prec, int n) {
             c->g_pcg32 = nullptr;
             cudaGraph_t gr;
             CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-            for (int i = 0; i < n; ++i) launch_pcg32_iter(c, c->cap_stream, prec, i & 1);
+            c->kslots[0] = 0;
+            for (int i = 0; i < n; ++i) {
+                cudaEvent_t e0 = nullptr, e1 = nullptr;
+                if (i % kSampleEvery == 0 && c->kslots[0] < to3d_ctx::kTimedSlots) {
+                    const int sl = c->kslots[0]++;
+                    e0 = c->kev[0][2 * sl];
+                    e1 = c->kev[0][2 * sl + 1];
+                    c->kslot_iter[0][sl] = i;
+                }
+                launch_pcg32_iter(c, c->cap_stream, prec, i & 1, e0, e1);
+            }
             CK(cudaStreamEndCapture(c->cap_stream, &gr));
             CK(cudaGraphInstantiate(&c->g_pcg32, gr, 0));
             cudaGraphDestroy(gr);
@@ -259,11 +300,13 @@ static to3d_status solve_f64(to3d_ctx* c, const double* f, double fnorm, to3d_so
         launch_ss_reset(c, c->stream, tol2, c->prm.cg_maxit - total);
         launch_pcg64_init(c, c->stream);
         LK("pcg64 init");
-        int n = 16;
+        int n = 16, it0 = 0;
         for (;;) {
             const int chunk_n = n < c->chunk ? n : c->chunk;
             if ((st = pcg64_chunk(c, chunk_n))) return st;
             if ((st = sync_scalars(c))) return st;
+            if (chunk_n == c->chunk) accumulate_kernel_times(c, 1, it0, c->ss_h->it);
+            it0 = c->ss_h->it;
             if (c->ss_h->done) break;
             if (n < c->chunk) n *= 2;
         }
@@ -305,11 +348,13 @@ static to3d_status solve_dc(to3d_ctx* c, const double* f, double fnorm, to3d_sol
         launch_ss_reset(c, c->stream, tol2_inner, c->prm.cg_maxit - total);
         launch_pcg32_init(c, c->stream, c->r, scale);
         LK("pcg32 init");
-        int n = 16;
+        int n = 16, it0 = 0;
         for (;;) {
             const int chunk_n = n < c->chunk ? n : c->chunk;
             if ((st = pcg32_chunk(c, prec, chunk_n))) return st;
             if ((st = sync_scalars(c))) return st;
+            if (chunk_n == c->chunk) accumulate_kernel_times(c, 0, it0, c->ss_h->it);
+            it0 = c->ss_h->it;
             if (c->ss_h->done) break;
             if (n < c->chunk) n *= 2;
         }
@@ -378,6 +423,18 @@ const char* to3d_last_error(const to3d_ctx* c) { return c ? c->err.c_str() : "nu
 
 int64_t to3d_launch_count(const to3d_ctx* c) { return c ? c->launches : 0; }
 
+to3d_status to3d_kernel_stats(to3d_ctx* c, int32_t which, double* ms_total, int64_t* samples,
+                              int32_t reset) {
+    if (!c || which < 0 || which > 1) return TO3D_EINVAL;
+    if (ms_total) *ms_total = c->kt_ms[which];
+    if (samples) *samples = c->kt_n[which];
+    if (reset) {
+        c->kt_ms[which] = 0.0;
+        c->kt_n[which] = 0;
+    }
+    return TO3D_OK;
+}
+
 to3d_status to3d_create(const to3d_params* prm, const uint8_t* fixed, const double* load,
                         const uint8_t* passive, void* stream, to3d_ctx** out) {
     if (!out) return TO3D_EINVAL;
@@ -420,14 +477,21 @@ to3d_status to3d_create(const to3d_params* prm, const uint8_t* fixed, const doub
 
 #define AL(ptr, n)                                        \
     if (dalloc(&(ptr), (size_t)(n)) != cudaSuccess) return fail(TO3D_ENOMEM);
-    AL(c->x, nel); AL(c->xnew, nel); AL(c->E, nel); AL(c->E32, nel);
+    c->pex = (g.nelx + 3) / 4 * 4;
+    const long long nel32 = (long long)c->pex * g.nely * g.nelz;
+    AL(c->x, nel); AL(c->xnew, nel); AL(c->E, nel); AL(c->E32, nel32);
     AL(c->ce, nel); AL(c->dc, nel); AL(c->dcf, nel); AL(c->Hs, nel);
     AL(c->ocq, nel); AL(c->oclo, nel); AL(c->ochi, nel); AL(c->passive, nel);
-    AL(c->nodemask, N); AL(c->dinv, N); AL(c->dinv32, N);
+    c->px = (g.nx + 3) / 4 * 4;
+    c->vol = (long long)c->px * g.ny * g.nz;
+    const long long vol = c->vol;
+    AL(c->nodemask, N); AL(c->dinv, N); AL(c->dinv32, vol); AL(c->maskp, vol);
     AL(c->f, ndof); AL(c->ftmp, ndof); AL(c->u, ndof); AL(c->r, ndof); AL(c->p, ndof);
     AL(c->q, ndof); AL(c->tmp, ndof);
-    AL(c->d32, ndof); AL(c->r32, ndof); AL(c->p32a, ndof); AL(c->p32b, ndof); AL(c->q32, ndof);
+    AL(c->d32, 3 * vol); AL(c->r32, 3 * vol); AL(c->p32a, 3 * vol); AL(c->p32b, 3 * vol);
+    AL(c->q32, 3 * vol);
     c->stage_slot = (size_t)(ndof > nel ? ndof : nel) * sizeof(double);
+    if ((size_t)(3 * vol) * sizeof(float) > c->stage_slot) c->stage_slot = (size_t)(3 * vol) * sizeof(float);
     c->stage_bytes = 4 * c->stage_slot;
     if (cudaMalloc(&c->stage, c->stage_bytes) != cudaSuccess) return fail(TO3D_ENOMEM);
     AL(c->red.partials, (size_t)kMaxReduceVals * kMaxBlocks);
@@ -440,8 +504,12 @@ to3d_status to3d_create(const to3d_params* prm, const uint8_t* fixed, const doub
         return fail(TO3D_ENOMEM);
     for (auto& ev : c->ev)
         if (cudaEventCreate(&ev) != cudaSuccess) return fail(TO3D_ECUDA);
+    for (auto& row : c->kev)
+        for (auto& ev : row)
+            if (cudaEventCreate(&ev) != cudaSuccess) return fail(TO3D_ECUDA);
     if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         return fail(TO3D_ECUDA);
+    if (!prepare_tc_operands(c)) return fail(TO3D_ECUDA);
 
     // host-side setup of inputs (copies; masks and initial design)
     std::vector<uint8_t> nm(N, 0);
@@ -467,6 +535,8 @@ to3d_status to3d_create(const to3d_params* prm, const uint8_t* fixed, const doub
         else ndesign++;
     }
     c->ndesign = ndesign;
+    std::vector<uint8_t> mp(vol, 0xff);
+    for (long long n = 0; n < N; ++n) mp[(n % g.nx) + (long long)c->px * (n / g.nx)] = nm[n];
     cudaStream_t s = c->stream;
     if (cudaMemcpyAsync(c->nodemask, nm.data(), N, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(c->f, fm.data(), ndof * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -475,8 +545,14 @@ to3d_status to3d_create(const to3d_params* prm, const uint8_t* fixed, const doub
         cudaMemsetAsync(c->red.counter, 0, sizeof(unsigned), s) != cudaSuccess ||
         cudaMemsetAsync(c->dev_err, 0, sizeof(int), s) != cudaSuccess ||
         cudaMemsetAsync(c->u, 0, ndof * 8, s) != cudaSuccess ||
-        cudaMemsetAsync(c->p32a, 0, ndof * 4, s) != cudaSuccess ||
-        cudaMemsetAsync(c->p32b, 0, ndof * 4, s) != cudaSuccess)
+        cudaMemcpyAsync(c->maskp, mp.data(), vol, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(c->dinv32, 0, vol * 4, s) != cudaSuccess ||
+        cudaMemsetAsync(c->E32, 0, nel32 * 4, s) != cudaSuccess ||
+        cudaMemsetAsync(c->d32, 0, 3 * vol * 4, s) != cudaSuccess ||
+        cudaMemsetAsync(c->r32, 0, 3 * vol * 4, s) != cudaSuccess ||
+        cudaMemsetAsync(c->q32, 0, 3 * vol * 4, s) != cudaSuccess ||
+        cudaMemsetAsync(c->p32a, 0, 3 * vol * 4, s) != cudaSuccess ||
+        cudaMemsetAsync(c->p32b, 0, 3 * vol * 4, s) != cudaSuccess)
         return fail(TO3D_ECUDA);
     launch_hs(c, s);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
@@ -554,8 +630,9 @@ to3d_status to3d_matvec_lowp(to3d_ctx* c, const double* x, const float* p, float
     if ((st = prepare_operator(c, (const double*)dx))) return st;
     float* dy = on_device ? y : (float*)((char*)c->stage + 2 * c->stage_slot);
     CK(cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
-    launch_matvec_tc(c, c->stream, c->E32, (const float*)dp, nullptr, nullptr, nullptr, dy, prec,
-                     false);
+    launch_aos_to_soa(c, c->stream, (const float*)dp, c->p32a);
+    launch_matvec_tc(c, c->stream, prec, false, 0);
+    launch_soa_to_aos(c, c->stream, c->q32, (const float*)dp, dy);
     LK("matvec_tc");
     int herr = 0;
     CK(cudaMemcpyAsync(&herr, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));

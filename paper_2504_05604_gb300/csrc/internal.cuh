@@ -1,6 +1,7 @@
 // Internal declarations of the to3d CUDA library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -89,7 +90,7 @@ struct to3d_ctx {
 
     // design / element arrays [nel]
     double *x = nullptr, *xnew = nullptr, *E = nullptr;
-    float* E32 = nullptr;
+    float* E32 = nullptr;                 // FP32 moduli, x extent padded to pex (pads 0)
     double *ce = nullptr, *dc = nullptr, *dcf = nullptr, *Hs = nullptr;
     double *ocq = nullptr, *oclo = nullptr, *ochi = nullptr;
     uint8_t* passive = nullptr;
@@ -105,6 +106,18 @@ struct to3d_ctx {
     void* stage = nullptr;
     size_t stage_bytes = 0, stage_slot = 0;
     int* dev_err = nullptr;               // device error word of the tensor-core kernels
+    // padded structure-of-arrays layout of the FP32 inner-solve vectors:
+    // component c of node (i,j,k) at c*vol + i + px*(j + ny*k), px = nx rounded up to 4
+    int px = 0;
+    long long vol = 0;
+    uint8_t* maskp = nullptr;             // [vol] clamp bits per padded node (pads: 0xff)
+    int pex = 0;                          // x extent of E32, nelx rounded up to 4
+    CUtensorMap tm_r, tm_pa, tm_pb, tm_d, tm_e;   // TMA descriptors of r32, p32a, p32b, dinv32, E32
+    uint8_t* tcB = nullptr;               // tensor-core B operand images (BF16 then FP16)
+    bool tc_split = false;                // B = [A_lam; A_mu] (N = 48) instead of one matrix
+    float tc_cscale = 1.f;                // scale of the combined integer B
+    int tc_lz = 20;                       // node layers per z segment of a tile
+    int tc_grid = 608;                    // persistent CTAs
     long long ndesign = 0;                // number of design (non-passive) elements
 
     to3d::Reducer red;
@@ -117,6 +130,14 @@ struct to3d_ctx {
     double fnorm = 0.0;
 
     cudaEvent_t ev[8] = {};
+    // sampled per-launch timing of the dominant kernels (event-record nodes
+    // inside the captured solver chunks): [0] tensor-core matvec, [1] FP64 matvec
+    static constexpr int kTimedSlots = 16;
+    cudaEvent_t kev[2][2 * kTimedSlots] = {};
+    int kslot_iter[2][kTimedSlots] = {};     // chunk-local iteration of each sample
+    int kslots[2] = {0, 0};
+    double kt_ms[2] = {0.0, 0.0};
+    long long kt_n[2] = {0, 0};
     cudaGraphExec_t g_pcg64 = nullptr;    // chunk of FP64 PCG iterations
     cudaGraphExec_t g_pcg32 = nullptr;    // chunk of inner FP32 PCG iterations
     int g_pcg32_prec = -1;
@@ -141,9 +162,11 @@ void launch_residual64(to3d_ctx* c, cudaStream_t s, const double* f, const doubl
 
 // pcg.cu
 void launch_pcg64_init(to3d_ctx* c, cudaStream_t s);
-void launch_pcg64_iter(to3d_ctx* c, cudaStream_t s);
+void launch_pcg64_iter(to3d_ctx* c, cudaStream_t s, cudaEvent_t ev0 = nullptr,
+                       cudaEvent_t ev1 = nullptr);
 void launch_pcg32_init(to3d_ctx* c, cudaStream_t s, const double* r64, double scale);
-void launch_pcg32_iter(to3d_ctx* c, cudaStream_t s, int prec, int parity);
+void launch_pcg32_iter(to3d_ctx* c, cudaStream_t s, int prec, int parity,
+                       cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 void launch_axpy_d32(to3d_ctx* c, cudaStream_t s, double inv_scale);
 void launch_norm2(to3d_ctx* c, cudaStream_t s, const double* v, long long n, double* out);
 void launch_ss_reset(to3d_ctx* c, cudaStream_t s, double tol2, int maxit);
@@ -153,10 +176,11 @@ inline void launch_fill_zero(to3d_ctx*, cudaStream_t s, void* ptr, size_t bytes)
 void launch_mask_copy(to3d_ctx* c, cudaStream_t s, const double* src, double* dst);
 
 // matvec_tc.cu
-void launch_matvec_tc(to3d_ctx* c, cudaStream_t s, const float* E32, const float* p_old,
-                      const float* r, const float* dinv, float* p_new, float* q, int prec,
-                      bool fused_dir);
+void launch_matvec_tc(to3d_ctx* c, cudaStream_t s, int prec, bool fused, int parity);
+void launch_aos_to_soa(to3d_ctx* c, cudaStream_t s, const float* in, float* out);
+void launch_soa_to_aos(to3d_ctx* c, cudaStream_t s, const float* q, const float* p, float* y);
 void init_tc_attributes();
+bool prepare_tc_operands(to3d_ctx* c);
 
 // element.cu
 void launch_sensitivity(to3d_ctx* c, cudaStream_t s, const double* x, const double* u,

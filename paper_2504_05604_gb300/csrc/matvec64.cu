@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(MV_TX* MV_TY* MV_TZ)
 // preconditioned residual zero there.
 __global__ void k_diag(const Grid g, const double* __restrict__ E, double kdd,
                        const uint8_t* __restrict__ nodemask, double* __restrict__ dinv,
-                       float* __restrict__ dinv32) {
+                       float* __restrict__ dinv32, int px) {
     const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= g.nnode) return;
     const int i = n % g.nx, j = (n / g.nx) % g.ny, k = n / ((long long)g.nx * g.ny);
@@ -158,19 +158,20 @@ __global__ void k_diag(const Grid g, const double* __restrict__ E, double kdd,
     // keep 1/d and the clamped components are zeroed by the residual mask
     const double di = (m == 7 || !(d > 0.0)) ? 0.0 : 1.0 / d;
     dinv[n] = di;
-    dinv32[n] = (float)di;
+    dinv32[i + (long long)px * (j + (long long)g.ny * k)] = (float)di;   // padded layout
 }
 
 // E_e = Emin + x_e^p (E0 - Emin) (Section 2.3), FP64 and an FP32 copy.
-__global__ void k_simp(long long nel, const double* __restrict__ x, double penal, double E0,
-                       double Emin, double* __restrict__ E, float* __restrict__ E32) {
+__global__ void k_simp(long long nel, int nelx, int pex, const double* __restrict__ x,
+                       double penal, double E0, double Emin, double* __restrict__ E,
+                       float* __restrict__ E32) {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= nel) return;
     const double xe = x[e];
     const double xp = (penal == 3.0) ? xe * xe * xe : pow(xe, penal);
     const double v = Emin + xp * (E0 - Emin);
     E[e] = v;
-    E32[e] = (float)v;
+    E32[(e % nelx) + (long long)pex * (e / nelx)] = (float)v;   // padded rows
 }
 
 // r = f - Ku on free dofs (0 on clamped); optional grid sums of r.r into ss.
@@ -219,14 +220,14 @@ void launch_matvec64(to3d_ctx* c, cudaStream_t s, const double* E, const double*
 void launch_diag(to3d_ctx* c, cudaStream_t s, const double* E) {
     const Grid& g = c->g;
     k_diag<<<(unsigned)((g.nnode + 255) / 256), 256, 0, s>>>(g, E, c->ke.v[0], c->nodemask,
-                                                             c->dinv, c->dinv32);
+                                                             c->dinv, c->dinv32, c->px);
     c->launches++;
 }
 
 void launch_simp(to3d_ctx* c, cudaStream_t s, const double* x) {
     const Grid& g = c->g;
-    k_simp<<<(unsigned)((g.nel + 255) / 256), 256, 0, s>>>(g.nel, x, c->prm.penal, c->prm.E0,
-                                                           c->prm.Emin, c->E, c->E32);
+    k_simp<<<(unsigned)((g.nel + 255) / 256), 256, 0, s>>>(g.nel, g.nelx, c->pex, x, c->prm.penal,
+                                                           c->prm.E0, c->prm.Emin, c->E, c->E32);
     c->launches++;
 }
 

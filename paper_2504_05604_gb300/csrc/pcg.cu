@@ -125,11 +125,12 @@ __global__ void k_pcg64_dir(long long nnode, const double* __restrict__ r,
 }
 
 // ---------------------------------------------------------------- FP32 inner form
-// r32 = r64 * s (s = 1/||r64||_inf-ish scale chosen by the host: here s = 1 /
-// sqrt(rr/ndof), stored in ss->beta before init), d = 0, p_old = 0, beta = 0.
-// The first fused matvec then builds p = M^-1 r.  rz and rr of the scaled r.
-__global__ void k_pcg32_init(long long nnode, const double* __restrict__ r64, double scale,
-                             const float* __restrict__ dinv, float* __restrict__ r32,
+// Vectors on the padded structure-of-arrays node grid (component c of padded
+// node p at c*vol + p; pad nodes stay zero).
+// r32 = r64 * scale (the host picks scale = 1/RMS(r64)), d = 0, p_old = 0;
+// the first fused matvec then builds p = M^-1 r.  rz and rr of the scaled r.
+__global__ void k_pcg32_init(const Grid g, int px, long long vol, const double* __restrict__ r64,
+                             double scale, const float* __restrict__ dinv, float* __restrict__ r32,
                              float* __restrict__ d32, float* __restrict__ p_old,
                              const Reducer red, SolverScalars* ss) {
     __shared__ double sh[64];
@@ -137,15 +138,15 @@ __global__ void k_pcg32_init(long long nnode, const double* __restrict__ r64, do
     float rz = 0.f, rr = 0.f;
     double rzd = 0.0, rrd = 0.0;
     int cnt = 0;
-    for (long long n = gtid(); n < nnode; n += gstride()) {
-        const float di = dinv[n];
+    for (long long n = gtid(); n < g.nnode; n += gstride()) {
+        const long long pp = (n % g.nx) + (long long)px * (n / g.nx);
+        const float di = dinv[pp];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const long long d = 3 * n + c;
-            const float rv = (float)(r64[d] * scale);
-            r32[d] = rv;
-            d32[d] = 0.f;
-            p_old[d] = 0.f;
+            const float rv = (float)(r64[3 * n + c] * scale);
+            r32[c * vol + pp] = rv;
+            d32[c * vol + pp] = 0.f;
+            p_old[c * vol + pp] = 0.f;
             rz = fmaf(di * rv, rv, rz);
             rr = fmaf(rv, rv, rr);
         }
@@ -167,33 +168,60 @@ __global__ void k_pcg32_init(long long nnode, const double* __restrict__ r64, do
     }
 }
 
-// d += alpha p, r -= alpha q, rz_new, rr, beta, flags
-__global__ void k_pcg32_update(long long nnode, float* __restrict__ d32, float* __restrict__ r32,
-                               const float* __restrict__ p, const float* __restrict__ q,
-                               const float* __restrict__ dinv, const Reducer red,
-                               SolverScalars* ss) {
+// d += alpha p, r -= alpha q (clamped dofs and pads kept at 0), rz_new, rr,
+// beta, flags.  Four consecutive nodes per step (vol is a multiple of 4), so
+// every thread keeps 14 independent 16-byte loads in flight.
+__global__ void __launch_bounds__(256)
+    k_pcg32_update(long long vol, float* __restrict__ d32, float* __restrict__ r32,
+                   const float* __restrict__ p, const float* __restrict__ q,
+                   const float* __restrict__ dinv, const uint8_t* __restrict__ maskp,
+                   const Reducer red, SolverScalars* ss) {
     if (ss->done) return;
     __shared__ double sh[64];
     __shared__ double out[2];
     const float alpha = (float)ss->alpha;
-    float rz = 0.f, rr = 0.f;
+    const long long v4 = vol >> 2;
+    float4* d4 = reinterpret_cast<float4*>(d32);
+    float4* r4 = reinterpret_cast<float4*>(r32);
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+    const float4* q4 = reinterpret_cast<const float4*>(q);
+    const float4* di4 = reinterpret_cast<const float4*>(dinv);
+    const uchar4* m4 = reinterpret_cast<const uchar4*>(maskp);
     double rzd = 0.0, rrd = 0.0;
-    int cnt = 0;
-    for (long long n = gtid(); n < nnode; n += gstride()) {
-        const float di = dinv[n];
+    for (long long n = gtid(); n < v4; n += gstride()) {
+        const float4 di = __ldg(di4 + n);
+        const uchar4 mk = __ldg(m4 + n);
+        float4 dd[3], pp[3], qq[3], rr[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const long long d = 3 * n + c;
-            d32[d] = fmaf(alpha, p[d], d32[d]);
-            const float rv = fmaf(-alpha, q[d], r32[d]);
-            r32[d] = rv;
-            rz = fmaf(di * rv, rv, rz);
-            rr = fmaf(rv, rv, rr);
+            dd[c] = d4[c * v4 + n];
+            pp[c] = __ldg(p4 + c * v4 + n);
+            qq[c] = __ldg(q4 + c * v4 + n);
+            rr[c] = r4[c * v4 + n];
         }
-        if (++cnt == 16) { rzd += rz; rrd += rr; rz = rr = 0.f; cnt = 0; }
+        float rz = 0.f, rs = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            dd[c].x = fmaf(alpha, pp[c].x, dd[c].x);
+            dd[c].y = fmaf(alpha, pp[c].y, dd[c].y);
+            dd[c].z = fmaf(alpha, pp[c].z, dd[c].z);
+            dd[c].w = fmaf(alpha, pp[c].w, dd[c].w);
+            float4 rv;
+            rv.x = ((mk.x >> c) & 1) ? 0.f : fmaf(-alpha, qq[c].x, rr[c].x);
+            rv.y = ((mk.y >> c) & 1) ? 0.f : fmaf(-alpha, qq[c].y, rr[c].y);
+            rv.z = ((mk.z >> c) & 1) ? 0.f : fmaf(-alpha, qq[c].z, rr[c].z);
+            rv.w = ((mk.w >> c) & 1) ? 0.f : fmaf(-alpha, qq[c].w, rr[c].w);
+            d4[c * v4 + n] = dd[c];
+            r4[c * v4 + n] = rv;
+            rz = fmaf(di.x * rv.x, rv.x, rz);
+            rz = fmaf(di.y * rv.y, rv.y, rz);
+            rz = fmaf(di.z * rv.z, rv.z, rz);
+            rz = fmaf(di.w * rv.w, rv.w, rz);
+            rs = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, fmaf(rv.w, rv.w, rs))));
+        }
+        rzd += rz;
+        rrd += rs;
     }
-    rzd += rz;
-    rrd += rr;
     double v[2] = {rzd, rrd};
     if (grid_sum<2>(red, v, sh, out) && threadIdx.x == 0) {
         const double rzn = out[0];
@@ -214,9 +242,13 @@ __global__ void k_pcg32_update(long long nnode, float* __restrict__ d32, float* 
 }
 
 // u64 += d32 / scale (FP64 accumulation of the correction)
-__global__ void k_axpy_d32(long long ndof, double* __restrict__ u, const float* __restrict__ d32,
-                           double inv_scale) {
-    for (long long d = gtid(); d < ndof; d += gstride()) u[d] = fma((double)d32[d], inv_scale, u[d]);
+__global__ void k_axpy_d32(const Grid g, int px, long long vol, double* __restrict__ u,
+                           const float* __restrict__ d32, double inv_scale) {
+    for (long long n = gtid(); n < g.nnode; n += gstride()) {
+        const long long pp = (n % g.nx) + (long long)px * (n / g.nx);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) u[3 * n + c] = fma((double)d32[c * vol + pp], inv_scale, u[3 * n + c]);
+    }
 }
 
 __global__ void k_norm2(long long n, const double* __restrict__ v, const Reducer red,
@@ -242,8 +274,10 @@ void launch_pcg64_init(to3d_ctx* c, cudaStream_t s) {
     c->launches++;
 }
 
-void launch_pcg64_iter(to3d_ctx* c, cudaStream_t s) {
+void launch_pcg64_iter(to3d_ctx* c, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+    if (ev0) cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal);
     launch_matvec64(c, s, c->E, c->p, c->q, true);
+    if (ev1) cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal);
     k_pcg64_update<<<vec_blocks(c->g.nnode), PCG_THREADS, 0, s>>>(c->g.nnode, c->u, c->r, c->p,
                                                                    c->q, c->dinv, c->red, c->ss);
     k_pcg64_dir<<<vec_blocks(c->g.nnode), PCG_THREADS, 0, s>>>(c->g.nnode, c->r, c->dinv, c->p,
@@ -253,23 +287,27 @@ void launch_pcg64_iter(to3d_ctx* c, cudaStream_t s) {
 
 void launch_pcg32_init(to3d_ctx* c, cudaStream_t s, const double* r64, double scale) {
     k_pcg32_init<<<vec_blocks(c->g.nnode), PCG_THREADS, 0, s>>>(
-        c->g.nnode, r64, scale, c->dinv32, c->r32, c->d32, c->p32b, c->red, c->ss);
+        c->g, c->px, c->vol, r64, scale, c->dinv32, c->r32, c->d32, c->p32b, c->red, c->ss);
     c->launches++;
 }
 
 // parity 0: p_old = p32b -> p_new = p32a; parity 1: the reverse.
-void launch_pcg32_iter(to3d_ctx* c, cudaStream_t s, int prec, int parity) {
-    float* p_old = parity ? c->p32a : c->p32b;
+// ev0/ev1 (may be null): external events recorded around the matvec launch.
+void launch_pcg32_iter(to3d_ctx* c, cudaStream_t s, int prec, int parity, cudaEvent_t ev0,
+                       cudaEvent_t ev1) {
     float* p_new = parity ? c->p32b : c->p32a;
-    launch_matvec_tc(c, s, c->E32, p_old, c->r32, c->dinv32, p_new, c->q32, prec, true);
-    k_pcg32_update<<<vec_blocks(c->g.nnode), PCG_THREADS, 0, s>>>(
-        c->g.nnode, c->d32, c->r32, p_new, c->q32, c->dinv32, c->red, c->ss);
+    if (ev0) cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal);
+    launch_matvec_tc(c, s, prec, true, parity);
+    if (ev1) cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal);
+    k_pcg32_update<<<vec_blocks(c->vol / 4), PCG_THREADS, 0, s>>>(c->vol, c->d32, c->r32, p_new,
+                                                              c->q32, c->dinv32, c->maskp, c->red,
+                                                              c->ss);
     c->launches++;
 }
 
 void launch_axpy_d32(to3d_ctx* c, cudaStream_t s, double inv_scale) {
-    const long long ndof = 3 * c->g.nnode;
-    k_axpy_d32<<<vec_blocks(ndof), PCG_THREADS, 0, s>>>(ndof, c->u, c->d32, inv_scale);
+    k_axpy_d32<<<vec_blocks(c->g.nnode), PCG_THREADS, 0, s>>>(c->g, c->px, c->vol, c->u, c->d32,
+                                                               inv_scale);
     c->launches++;
 }
 

@@ -15,7 +15,7 @@ from tests.gpu_helpers import emulate_lowp, lib_ctx, random_problem
 
 pytestmark = pytest.mark.gpu
 
-SIZES = [(1, 1, 1), (3, 2, 2), (16, 8, 8), (31, 9, 8), (33, 5, 3), (60, 20, 4)]
+SIZES = [(1, 1, 1), (3, 2, 2), (16, 8, 8), (31, 9, 8), (33, 5, 3), (60, 20, 4), (20, 6, 45)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -60,13 +60,17 @@ def test_matvec64_device_pointers():
     assert np.array_equal(yd.cpu().numpy(), y)
 
 
+@pytest.mark.parametrize("nu", [0.3, 0.33])
 @pytest.mark.parametrize("prec,tol_exact", [(1, 2.0 ** -8), (2, 2.0 ** -16), (3, 2.0 ** -10)])
 @pytest.mark.parametrize("dims", SIZES)
-def test_matvec_tensor_core(dims, prec, tol_exact):
+def test_matvec_tensor_core(dims, prec, tol_exact, nu):
+    # nu = 0.3 uses one combined integer B (3 A_lam + 2 A_mu); nu = 0.33 has
+    # no small rational lam/mu and exercises the split B = [A_lam; A_mu]
     prob = random_problem(*dims, seed=7 + sum(dims))
+    prob.nu = nu
     x = problems.random_density(prob.nel, 8, 0.0, 1.0)
     p32 = problems.random_vector(prob.ndof, 9).astype(np.float32)
-    ctx = lib_ctx(prob)
+    ctx = lib_ctx(prob, nu=nu)
     y = ctx.matvec_lowp(x, p32, prec).astype(np.float64)
     y_emul, bound = emulate_lowp(prob, x, p32, prec)
     free = prob.fixed == 0
