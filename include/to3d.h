@@ -200,6 +200,34 @@ TO3D_API to3d_status to3d_oc_update(to3d_ctx* ctx, const double* x, const double
                            double* lambda, double* volume, int32_t* halvings,
                            int32_t on_device);
 
+/* Same results as to3d_sensitivity, but the library allocates nothing, and
+ * no context is needed.  The paper has no counterpart: this entry point
+ * exists for callers that cannot let a library call cudaMalloc.  Examples are
+ * programs whose own pool or arena holds all device memory, where an outside
+ * allocation falls outside that budget and may fail, and latency-critical
+ * loops that must not enter the driver's allocator, which can synchronise the
+ * device.
+ *   x [nel], u [3N]       device pointers, inputs (densities, displacements)
+ *   ce, dc [nel]          device pointers, outputs
+ *   *compliance           host pointer, output
+ *   stream                cudaStream_t (as void*) the work is enqueued on;
+ *                         the call returns after the stream has finished it.
+ * The grid-wide compliance sum uses one fixed scratch array compiled into
+ * the library: 256 KiB + 256 B, which every GPU that loads the library
+ * holds until the process exits.  It limits nel to 8,388,608 elements
+ * (32768 blocks of 256); larger grids return TO3D_EINVAL, as do non-positive
+ * sizes, null pointers and out-of-range parameters.  The first call on each
+ * device looks up the array's device address; make that first call before
+ * any stream capture.  All calls share the array, and each call leaves its
+ * contents behind (the call clears what must start at zero), so calls that
+ * overlap on the GPU -- on different streams or from different threads --
+ * race on it and must be serialised by the caller.
+ * Errors: TO3D_EINVAL as above, TO3D_ECUDA if a CUDA call fails. */
+TO3D_API to3d_status to3d_sensitivity_noalloc(int32_t nelx, int32_t nely, int32_t nelz,
+                                              double penal, double E0, double Emin, double nu,
+                                              const double* x, const double* u, double* ce,
+                                              double* dc, double* compliance, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

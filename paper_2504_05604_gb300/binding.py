@@ -84,6 +84,8 @@ _SIGS = {
     "to3d_sensitivity": (I32, [VP, VP, VP, VP, VP, DP, I32]),
     "to3d_filter_apply": (I32, [VP, I32, VP, VP, VP, I32, I32]),
     "to3d_oc_update": (I32, [VP, VP, VP, VP, DP, DP, C.POINTER(I32), I32]),
+    "to3d_sensitivity_noalloc": (I32, [I32, I32, I32, C.c_double, C.c_double, C.c_double,
+                                       C.c_double, VP, VP, VP, VP, DP, VP]),
 }
 
 
@@ -295,3 +297,24 @@ class Context:
         self._check(self.lib.to3d_oc_update(self.h, ax.ptr, ad.ptr, an.ptr, C.byref(lam),
                                             C.byref(vol), C.byref(nh), dev), "oc_update")
         return xnew, lam.value, vol.value, nh.value
+
+
+def sensitivity_noalloc(nelx, nely, nelz, x, u, ce, dc, penal=3.0, E0=1.0, Emin=1e-9, nu=0.3,
+                        stream=None):
+    """Energies, sensitivities and compliance into caller-owned CUDA tensors
+    with no device allocation by the library (``to3d_sensitivity_noalloc``).
+    x, u are inputs and ce, dc outputs: contiguous CUDA float64 tensors.
+    Returns the compliance."""
+    args = [_Arg(t, np.float64) for t in (x, u, ce, dc)]
+    if any(a.dev != 1 for a in args):
+        raise TypeError("sensitivity_noalloc takes CUDA tensors only")
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    comp = C.c_double()
+    st = load().to3d_sensitivity_noalloc(nelx, nely, nelz, penal, E0, Emin, nu, args[0].ptr,
+                                         args[1].ptr, args[2].ptr, args[3].ptr, C.byref(comp),
+                                         VP(stream))
+    if st != 0:
+        raise To3dError(st, "to3d_sensitivity_noalloc")
+    return comp.value

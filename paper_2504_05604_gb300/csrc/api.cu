@@ -96,6 +96,19 @@ static bool build_ke(to3d_ctx* c) {
     return true;
 }
 
+// Unit-modulus KE for Poisson ratio nu (same derivation as build_ke).
+bool unit_ke(double nu, KE64* out) {
+    double Al[576], Am[576];
+    hex8_split(Al, Am);
+    const double lam = nu / ((1 + nu) * (1 - 2 * nu)), mu = 1.0 / (2 * (1 + nu));
+    for (int k = 0; k < 576; ++k) {
+        const double rl = std::nearbyint(Al[k]), rm = std::nearbyint(Am[k]);
+        if (std::fabs(rl - Al[k]) > 1e-9 || std::fabs(rm - Am[k]) > 1e-9) return false;
+        out->v[k] = lam / 72.0 * rl + mu / 72.0 * rm;
+    }
+    return true;
+}
+
 static bool build_stencil(to3d_ctx* c) {
     const double rmin = c->prm.rmin;
     const int R = (int)std::ceil(rmin);

@@ -253,6 +253,13 @@ void launch_sensitivity(to3d_ctx* c, cudaStream_t s, const double* x, const doub
     c->launches++;
 }
 
+void launch_sensitivity_raw(const KE64& ke, const Grid& g, cudaStream_t s, const double* x,
+                            const double* u, double penal, double E0, double Emin, double* ce,
+                            double* dc, const Reducer& red, double* comp_out) {
+    k_sensitivity<<<el_blocks(g.nel), EL_THREADS, 0, s>>>(ke, g, x, u, penal, E0, Emin, ce, dc, red,
+                                                          comp_out);
+}
+
 void launch_hs(to3d_ctx* c, cudaStream_t s) {
     k_hs<<<el_blocks(c->g.nel), EL_THREADS, 0, s>>>(*c->st, c->g, c->Hs);
     c->launches++;

@@ -186,6 +186,11 @@ bool prepare_tc_operands(to3d_ctx* c);
 void launch_sensitivity(to3d_ctx* c, cudaStream_t s, const double* x, const double* u,
                         double* ce, double* dc);
 void launch_hs(to3d_ctx* c, cudaStream_t s);
+void launch_sensitivity_raw(const KE64& ke, const Grid& g, cudaStream_t s, const double* x,
+                            const double* u, double penal, double E0, double Emin, double* ce,
+                            double* dc, const Reducer& red, double* comp_out);
+bool unit_ke(double nu, KE64* out);
+constexpr int kElementThreads = 256;   // threads per block of the element kernels
 void launch_filter(to3d_ctx* c, cudaStream_t s, int mode, const double* a, const double* b,
                    double* out);
 void launch_oc_begin(to3d_ctx* c, cudaStream_t s, const double* x, const double* dcf,
