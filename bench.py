@@ -29,7 +29,7 @@ if ROOT not in sys.path:
 
 METRIC = "OC iters/s at 480x160x80, chosen vs plain FP64 Jacobi-PCG at rel.res 1e-8"
 UNIT = "OC iters/s"
-PREC_NAMES = {0: "fp64", 1: "bf16-dc", 2: "bf16x2-dc", 3: "fp16-dc"}
+PREC_NAMES = {0: "fp64", 1: "bf16-dc", 2: "bf16x2-dc", 3: "fp16-dc", 4: "fp16x2-dc"}
 # Jacobi-PCG iterations per OC iteration used to turn the oracle's measured
 # per-iteration cost into OC iterations/s when no GPU run in the same process
 # supplies the count (reference arm): the mean CG iteration count of OC
@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", type=int, default=2, help="0 fp64, 1 bf16, 2 bf16x2, 3 fp16")
     ap.add_argument("--size", default="480x160x80")
+    ap.add_argument("--inner-rtol", type=float, default=0.3,
+                    help="residual-replacement factor of the defect-correction forms")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison step")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -229,7 +231,8 @@ def ours(args):
     nelx, nely, nelz = dims(args)
     prob = problems.config_large(nelx=nelx, nely=nely, nelz=nelz)
     stream = torch.cuda.Stream(device=dev)
-    ctx = Context.from_problem(prob, precision=args.precision, stream=stream.cuda_stream)
+    ctx = Context.from_problem(prob, precision=args.precision, stream=stream.cuda_stream,
+                               inner_rtol=args.inner_rtol)
     warm = [ctx.step() for _ in range(args.warmup)]
 
     def barrier():

@@ -65,7 +65,8 @@ typedef enum {
     TO3D_F64 = 0,        /* FP64 Jacobi-PCG with the FP64 element matvec      */
     TO3D_BF16_DC = 1,    /* BF16 operand (one slice)                          */
     TO3D_BF16X2_DC = 2,  /* BF16 hi + lo slices (about 16 mantissa bits)      */
-    TO3D_FP16_DC = 3     /* FP16 operand with per-element power-of-two scale  */
+    TO3D_FP16_DC = 3,    /* FP16 operand with per-element power-of-two scale  */
+    TO3D_FP16X2_DC = 4   /* scaled FP16 hi + lo slices (about 22 bits)        */
 } to3d_precision;
 
 typedef enum { TO3D_JACOBI = 0, TO3D_CNN_FCG = 1 } to3d_precond;
@@ -80,7 +81,9 @@ typedef struct {
     double move;         /* OC move limit                                     */
     double bisect_tol;   /* stop bisection when (l2-l1)/(l1+l2) <= tol        */
     double cg_rtol;      /* stop when ||f - K u||_2 <= cg_rtol ||f||_2        */
-    double inner_rtol;   /* *_DC forms: inner solve relative tolerance        */
+    double inner_rtol;   /* *_DC forms: the FP32 residual is replaced by the  */
+                         /* true FP64 one each time it has dropped by this    */
+                         /* factor (0 < inner_rtol < 1)                       */
     int32_t cg_maxit;    /* iteration limit of one solve (all inner steps)    */
     int32_t filter;      /* to3d_filter                                       */
     int32_t precision;   /* to3d_precision                                    */
@@ -114,7 +117,7 @@ typedef struct to3d_ctx to3d_ctx;
 
 /* Fill *p with the defaults: E0 = 1, Emin = 1e-9, nu = 0.3, penal = 3,
  * volfrac = 0.3, rmin = 1.5, move = 0.2, bisect_tol = 1e-3, cg_rtol = 1e-8,
- * inner_rtol = 1e-4, cg_maxit = 200000, sensitivity filter, TO3D_F64,
+ * inner_rtol = 0.3, cg_maxit = 200000, sensitivity filter, TO3D_F64,
  * Jacobi, oc_levels = 3, warm_start = 1.  Grid sizes are set to 0. */
 TO3D_API to3d_status to3d_default_params(to3d_params* p);
 
@@ -165,7 +168,7 @@ TO3D_API to3d_status to3d_matvec(to3d_ctx* ctx, const double* x, const double* p
                         int32_t on_device);
 
 /* y = Kbar(x) p with the tensor-core element matvec of precision `prec`
- * (TO3D_BF16_DC, TO3D_BF16X2_DC or TO3D_FP16_DC): p rounded per element to
+ * (TO3D_BF16_DC, TO3D_BF16X2_DC, TO3D_FP16_DC or TO3D_FP16X2_DC): p rounded per element to
  * the 16-bit operand format, integer-exact element stiffness, FP32
  * accumulation, FP32 scaling by E_e.  p, y [3N] FP32. */
 TO3D_API to3d_status to3d_matvec_lowp(to3d_ctx* ctx, const double* x, const float* p, float* y,

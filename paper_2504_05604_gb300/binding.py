@@ -19,7 +19,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libto3d.so")
 
-F64, BF16_DC, BF16X2_DC, FP16_DC = 0, 1, 2, 3
+F64, BF16_DC, BF16X2_DC, FP16_DC, FP16X2_DC = 0, 1, 2, 3, 4
 JACOBI, CNN_FCG = 0, 1
 FILTER_SENS, FILTER_DENS = 0, 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error",

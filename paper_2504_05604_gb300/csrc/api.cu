@@ -4,6 +4,7 @@
 // few device scalars per solve chunk and fills the iteration record.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -338,51 +339,91 @@ static to3d_status solve_f64(to3d_ctx* c, const double* f, double fnorm, to3d_so
     return TO3D_OK;
 }
 
-// FP64 defect correction around an FP32 inner PCG with the tensor-core matvec.
+// FP64 defect correction around one FP32 inner PCG with the tensor-core
+// matvec.  The inner CG is not restarted: whenever its recurrence residual
+// has dropped by the factor delta (= inner_rtol) since the last replacement,
+// u absorbs the correction d in FP64, the true residual f - K u is formed in
+// FP64 and replaces the FP32 residual, and the CG continues from its last
+// search direction, re-orthogonalised against the new residual.  The solve
+// ends when the true relative residual is <= cg_rtol.
 static to3d_status solve_dc(to3d_ctx* c, const double* f, double fnorm, to3d_solve_info* info) {
     const double tol = c->prm.cg_rtol;
+    const double delta = c->prm.inner_rtol;
     const int prec = c->prm.precision;
     const long long ndof = 3 * c->g.nnode;
-    int total = 0, outer = 0, status = TO3D_OK;
+    int total = 0, outer = 0, status = TO3D_OK, stalls = 0;
     double relres = 0.0;
     to3d_status st;
-    for (;;) {
-        if ((st = true_residual(c, f, fnorm, &relres))) return st;
-        if (relres <= tol || fnorm == 0.0) break;
-        if (outer >= 40 || total >= c->prm.cg_maxit) {
-            status = TO3D_ENOCONV;
-            break;
-        }
-        // normalise the defect to unit RMS so FP32 has headroom both ways
-        const double rr = c->ss_h->rr_true;
-        const double scale = 1.0 / std::sqrt(rr / (double)ndof);
-        const double eta = std::fmax(c->prm.inner_rtol, 0.5 * tol / relres);
-        const double tol2_inner = eta * eta * (double)ndof;
-        launch_ss_reset(c, c->stream, tol2_inner, c->prm.cg_maxit - total);
+    if ((st = true_residual(c, f, fnorm, &relres))) return st;
+    if (relres > tol && fnorm > 0.0) {
+        // unit-RMS scaling of the inner system, fixed for the whole solve
+        const double scale = 1.0 / std::sqrt(c->ss_h->rr_true / (double)ndof);
+        const double relres0 = relres;
+        const double t = 0.5 * tol * fnorm * scale;
+        const double target2 = t * t;
+        launch_ss_reset(c, c->stream, std::fmax(delta * delta * (double)ndof, target2), c->prm.cg_maxit);
         launch_pcg32_init(c, c->stream, c->r, scale);
         LK("pcg32 init");
-        int n = 16, it0 = 0;
         for (;;) {
-            const int chunk_n = n < c->chunk ? n : c->chunk;
-            if ((st = pcg32_chunk(c, prec, chunk_n))) return st;
-            if ((st = sync_scalars(c))) return st;
-            if (chunk_n == c->chunk) accumulate_kernel_times(c, 0, it0, c->ss_h->it);
-            it0 = c->ss_h->it;
-            if (c->ss_h->done) break;
-            if (n < c->chunk) n *= 2;
+            int n = 16, it0 = 0;
+            for (;;) {
+                const int chunk_n = n < c->chunk ? n : c->chunk;
+                if ((st = pcg32_chunk(c, prec, chunk_n))) return st;
+                if ((st = sync_scalars(c))) return st;
+                if (chunk_n == c->chunk) accumulate_kernel_times(c, 0, it0, c->ss_h->it);
+                it0 = c->ss_h->it;
+                if (c->ss_h->done) break;
+                if (n < c->chunk) n *= 2;
+            }
+            const int its = c->ss_h->it;
+            total += its;
+            if (c->ss_h->status == TO3D_ETIMEOUT || c->ss_h->status == TO3D_ENUMERIC) {
+                status = c->ss_h->status;
+                break;
+            }
+            launch_axpy_d32(c, c->stream, 1.0 / scale);
+            LK("axpy");
+            const double prev = relres;
+            if ((st = true_residual(c, f, fnorm, &relres))) return st;
+            if (c->trace)
+                std::fprintf(stderr, "to3d: segment %d: %d inner its (total %d), relres %.3e -> %.3e\n",
+                             outer, its, total, prev, relres);
+            if (relres <= tol) break;
+            if (total >= c->prm.cg_maxit || outer >= 1000) {
+                status = TO3D_ENOCONV;
+                break;
+            }
+            outer++;
+            if (relres > 0.5 * prev) {
+                // the recurrence residual ran away from the true one (too
+                // coarse an operand): restart the inner CG from the true
+                // residual instead of keeping its direction
+                if (++stalls > 50) {
+                    status = TO3D_ENOCONV;
+                    break;
+                }
+                launch_ss_reset(c, c->stream,
+                                std::fmax(delta * delta * (double)ndof * (relres / relres0) *
+                                              (relres / relres0),
+                                          target2),
+                                c->prm.cg_maxit - total);
+                launch_pcg32_init(c, c->stream, c->r, scale);
+                LK("pcg32 restart");
+                continue;
+            }
+            // the last direction is in p32a after an odd number of fused
+            // iterations; the captured chunks read p_old from p32b first
+            if (its & 1)
+                CK(cudaMemcpyAsync(c->p32b, c->p32a, sizeof(float) * 3 * c->vol,
+                                   cudaMemcpyDeviceToDevice, c->stream));
+            launch_ss_segment(c, c->stream, target2, c->prm.cg_maxit - total);
+            launch_pcg32_replace(c, c->stream, c->r, scale, c->p32b, delta * delta, target2);
+            LK("residual replacement");
         }
-        total += c->ss_h->it;
-        outer++;
-        if (c->ss_h->status == TO3D_ETIMEOUT || c->ss_h->status == TO3D_ENUMERIC) {
-            status = c->ss_h->status;
-            break;
-        }
-        launch_axpy_d32(c, c->stream, 1.0 / scale);
-        LK("axpy");
     }
     if (info) {
         info->iters = total;
-        info->outer = outer;
+        info->outer = outer + 1;
         info->status = status;
         info->relres = relres;
     }
@@ -420,7 +461,7 @@ to3d_status to3d_default_params(to3d_params* p) {
     p->move = 0.2;
     p->bisect_tol = 1e-3;
     p->cg_rtol = 1e-8;
-    p->inner_rtol = 1e-4;
+    p->inner_rtol = 0.3;
     p->cg_maxit = 200000;
     p->filter = TO3D_FILTER_SENS;
     p->precision = TO3D_F64;
@@ -460,14 +501,15 @@ to3d_status to3d_create(const to3d_params* prm, const uint8_t* fixed, const doub
         !(prm->E0 > 0) || !(prm->Emin > 0) || !(prm->Emin < prm->E0) || !(prm->nu > -1) ||
         !(prm->nu < 0.5) || !(prm->move > 0) || !(prm->bisect_tol > 0) || !(prm->cg_rtol > 0) ||
         prm->cg_maxit < 1 || prm->oc_levels < 1 || prm->oc_levels > 5 || prm->precision < 0 ||
-        prm->precision > 3 || prm->filter < 0 || prm->filter > 1)
+        prm->precision > 4 || prm->filter < 0 || prm->filter > 1)
         return TO3D_EINVAL;
     if (prm->precond != TO3D_JACOBI) return TO3D_EINVAL;
 
     to3d_ctx* c = new (std::nothrow) to3d_ctx();
     if (!c) return TO3D_ENOMEM;
     c->prm = *prm;
-    if (c->prm.inner_rtol <= 0) c->prm.inner_rtol = 1e-4;
+    c->trace = std::getenv("TO3D_TRACE") != nullptr;   // per-segment solver log on stderr
+    if (!(c->prm.inner_rtol > 0 && c->prm.inner_rtol < 1)) c->prm.inner_rtol = 0.3;
     c->stream = (cudaStream_t)stream;
     Grid& g = c->g;
     g.nelx = prm->nelx; g.nely = prm->nely; g.nelz = prm->nelz;
@@ -633,7 +675,8 @@ to3d_status to3d_matvec(to3d_ctx* c, const double* x, const double* p, double* y
 to3d_status to3d_matvec_lowp(to3d_ctx* c, const double* x, const float* p, float* y, int32_t prec,
                              int32_t on_device) {
     if (!c || !x || !p || !y) return TO3D_EINVAL;
-    if (prec != TO3D_BF16_DC && prec != TO3D_BF16X2_DC && prec != TO3D_FP16_DC)
+    if (prec != TO3D_BF16_DC && prec != TO3D_BF16X2_DC && prec != TO3D_FP16_DC &&
+        prec != TO3D_FP16X2_DC)
         return set_err(c, TO3D_EINVAL, "matvec_lowp: precision must be a tensor-core form");
     const size_t nb = c->g.nel * 8, db = 3 * c->g.nnode * 4;
     const void *dx, *dp;

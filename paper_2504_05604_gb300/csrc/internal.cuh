@@ -45,6 +45,8 @@ struct Stencil {
 // Device-resident solver / OC state, so loops need no host round trip.
 struct SolverScalars {
     double rz, rz_new, pq, rr, alpha, beta;
+    double zcoef;             // coefficient of M^-1 r in the next direction (1 except
+                              // right after a residual replacement)
     double fnorm2, tol2;
     double rr_true;
     int it, done, status, maxit;
@@ -81,6 +83,7 @@ struct to3d_ctx {
     std::string err;
     long long launches = 0;
     int iter = 0;
+    bool trace = false;
     bool have_u = false;
     bool have_dinv = false;
 
@@ -165,11 +168,14 @@ void launch_pcg64_init(to3d_ctx* c, cudaStream_t s);
 void launch_pcg64_iter(to3d_ctx* c, cudaStream_t s, cudaEvent_t ev0 = nullptr,
                        cudaEvent_t ev1 = nullptr);
 void launch_pcg32_init(to3d_ctx* c, cudaStream_t s, const double* r64, double scale);
+void launch_pcg32_replace(to3d_ctx* c, cudaStream_t s, const double* r64, double scale,
+                          const float* p_latest, double delta2, double target2);
 void launch_pcg32_iter(to3d_ctx* c, cudaStream_t s, int prec, int parity,
                        cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 void launch_axpy_d32(to3d_ctx* c, cudaStream_t s, double inv_scale);
 void launch_norm2(to3d_ctx* c, cudaStream_t s, const double* v, long long n, double* out);
 void launch_ss_reset(to3d_ctx* c, cudaStream_t s, double tol2, int maxit);
+void launch_ss_segment(to3d_ctx* c, cudaStream_t s, double tol2, int maxit);
 inline void launch_fill_zero(to3d_ctx*, cudaStream_t s, void* ptr, size_t bytes) {
     cudaMemsetAsync(ptr, 0, bytes, s);
 }

@@ -43,6 +43,7 @@
 //   1  BF16:    A = bf16(p_e)
 //   2  BF16X2:  A_hi = bf16(p_e), A_lo = bf16(p_e - A_hi); D accumulates both
 //   3  FP16:    p_e scaled by a power of two so max|p_e| lies in [2^10, 2^11)
+//   4  FP16X2:  the scaled p_e as FP16 hi + lo slices (about 22 significant bits)
 #include <cmath>
 #include <vector>
 
@@ -70,22 +71,8 @@ constexpr int TC_STAGE_BYTES = 5760;
 constexpr int TC_EBOX_BYTES = TC_BOXX * TC_EY * 4;   // 640 B
 constexpr int TC_STAGE_TX = 2 * TC_VEC_BYTES + TC_PLANE * 4 + TC_EBOX_BYTES;   // fused stage
 constexpr int TC_STAGE_TX_PLAIN = TC_VEC_BYTES + TC_EBOX_BYTES;
-constexpr int TC_ZSTRIDE = 36;                       // floats per element row of Z: 8 float4
-                                                     // slots (a+2b, c) + pad, conflict-free
 constexpr int TC_A_BYTES = 128 * 64;                 // one 128 x 32 16-bit operand tile
 static_assert(TC_EX * TC_EY == 128, "one element layer per MMA");
-
-template <int NSL, int NMMA>
-struct TcSmem {
-    static constexpr int STAGES = 0;                               // [NS] x 5120 B
-    static constexpr int A = STAGES + TC_NS * TC_STAGE_BYTES;      // [2][NSL] operand tiles
-    static constexpr int B = A + 2 * NSL * TC_A_BYTES;             // NMMA x 32 operand
-    static constexpr int Z = B + NMMA * 64;                        // [128][28] floats
-    static constexpr int BAR = Z + 128 * TC_ZSTRIDE * 4;           // NS + 2 mbarriers
-    static constexpr int TADDR = BAR + 8 * (TC_NS + 2);
-    static constexpr int USED = TADDR + 16;
-    static constexpr int BYTES = 1024 + USED;
-};
 
 __device__ __forceinline__ int kmaj_off(int row, int k) {
     return (row >> 3) * 512 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
@@ -167,7 +154,9 @@ constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
 
 // Warp roles: warps 0-3 build (direction update + A rows), warps 4-7 run the
 // epilogue (TMEM -> scaled rows -> node assembly), warp 8 lane 0 issues TMA,
-// warp 9 lane 0 issues the MMAs.  Hand-offs use mbarriers:
+// warp 9 lane 0 issues the MMAs.  (The two single-thread roles live in
+// different warps: a lane spinning on an mbarrier can hold up the rest of
+// its warp.)  Hand-offs use mbarriers:
 //   full[s]/empty[s]  node-layer stage s loaded / released (builders + epilogue)
 //   conv[s]           stage s holds the converted direction p_new
 //   afull/aempty[b]   A tile b written / consumed by the MMA
@@ -175,15 +164,16 @@ constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
 // Barrier phases follow running counters of node layers (G) and element
 // layers (H) that every role advances identically tile after tile.
 constexpr int TC_ROLE_THREADS = 320;
+constexpr int TC_CTAS_PER_SM = 3;
 
 template <int NSL, int NMMA>
 struct TcSmemWs {
-    static constexpr int NS = (NSL == 1) ? 12 : 9;                // ring stages
+    static constexpr int NS = (NSL == 1) ? 7 : 6;                 // ring stages
     static constexpr int STAGES = 0;
     static constexpr int A = STAGES + NS * TC_STAGE_BYTES;
     static constexpr int B = A + 2 * NSL * TC_A_BYTES;
-    static constexpr int Z = B + NMMA * 64;
-    static constexpr int BAR = Z + 128 * TC_ZSTRIDE * 4;
+    static constexpr int Z = B + NMMA * 64;                       // [4 warps][16][6] floats
+    static constexpr int BAR = Z + 4 * 16 * 6 * 4;
     static constexpr int NBAR = 3 * NS + 8;
     static constexpr int TADDR = BAR + 8 * NBAR;
     static constexpr int USED = TADDR + 16;
@@ -191,12 +181,13 @@ struct TcSmemWs {
 };
 
 template <int PREC, bool FUSED, bool SPLIT>
-__global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
+__global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
     k_matvec_tc(const __grid_constant__ TcArgs a, const __grid_constant__ CUtensorMap tm_r,
                 const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorMap tm_d,
                 const __grid_constant__ CUtensorMap tm_e) {
-    constexpr int NSL = (PREC == 2) ? 2 : 1;
-    constexpr bool BF = (PREC != 3);
+    constexpr int NSL = (PREC == 2 || PREC == 4) ? 2 : 1;
+    constexpr bool BF = (PREC == 1 || PREC == 2);
+    constexpr bool SCALED = (PREC == 3 || PREC == 4);
     constexpr int NMMA = SPLIT ? 64 : 32;            // split: A_lam rows, A_mu rows, 16 spare
     constexpr int TCOLS = SPLIT ? 64 : 32;           // TMEM columns per accumulator
     using L = TcSmemWs<NSL, NMMA>;
@@ -255,6 +246,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
     tc::tc_fence_after();
     const uint32_t tmem = *s_taddr;
     const float beta = FUSED ? (float)a.ss->beta : 0.f;
+    const float zcoef = FUSED ? (float)a.ss->zcoef : 1.f;
     constexpr uint32_t STAGE_TX = FUSED ? TC_STAGE_TX : TC_STAGE_TX_PLAIN;
     volatile int* vfail = &s_fail;
     double dot = 0.0;
@@ -349,10 +341,10 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                     const int c = idx / Q, rem = idx - c * Q;
                     const float4 d4 = D[rem], r4 = R[idx], p4 = P[idx];
                     float4 v;
-                    v.x = fmaf(d4.x, r4.x, beta * p4.x);
-                    v.y = fmaf(d4.y, r4.y, beta * p4.y);
-                    v.z = fmaf(d4.z, r4.z, beta * p4.z);
-                    v.w = fmaf(d4.w, r4.w, beta * p4.w);
+                    v.x = fmaf(zcoef * d4.x, r4.x, beta * p4.x);
+                    v.y = fmaf(zcoef * d4.y, r4.y, beta * p4.y);
+                    v.z = fmaf(zcoef * d4.z, r4.z, beta * p4.z);
+                    v.w = fmaf(zcoef * d4.w, r4.w, beta * p4.w);
                     P[idx] = v;
                     const int yy = rem / (TC_BOXX / 4), x0 = 4 * (rem - yy * (TC_BOXX / 4));
                     if (owned_layer && yy >= 1 && yy <= TC_BY) {
@@ -405,7 +397,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                     v[3 * bb + 2] = src[2 * TC_PLANE];
                 }
                 float code = 0.f;
-                if (PREC == 3) {
+                if (SCALED) {
                     float m = 0.f;
 #pragma unroll
                     for (int i = 0; i < 24; ++i) m = fmaxf(m, fabsf(v[i]));
@@ -425,12 +417,14 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                 }
                 uint8_t* At = sA + b * NSL * TC_A_BYTES;
                 store_row<BF>(At, tid, v);
-                if (PREC == 3)
+                if (SCALED)
                     *reinterpret_cast<uint4*>(At + kmaj_off(tid, 24)) = make_uint4(pack2<BF>(code, 0.f), 0u, 0u, 0u);
-                if (PREC == 2) {
+                if (NSL == 2) {
                     float r2[24];
 #pragma unroll
-                    for (int i = 0; i < 24; ++i) r2[i] = v[i] - __bfloat162float(__float2bfloat16_rn(v[i]));
+                    for (int i = 0; i < 24; ++i)
+                        r2[i] = BF ? v[i] - __bfloat162float(__float2bfloat16_rn(v[i]))
+                                   : v[i] - __half2float(__float2half_rn(v[i]));
                     store_row<BF>(At + TC_A_BYTES, tid, r2);
                 }
                 tc::fence_proxy_async_smem();
@@ -447,9 +441,9 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
         // ------------------------------------------------ epilogue (warps 4-7)
         const int et = tid - 128;                       // TMEM lane = element of the layer
         const int ei = et % TC_EX, ej = et / TC_EX;
-        const bool node_thread = et < TC_BX * TC_BY;
-        const int nli = 1 + et % TC_BX, nlj = 1 + et / TC_BX;
         const int ew = warp - 4;
+        // this lane finishes node (ei, 2 ew + 1 + upper-half) of every layer
+        const bool node_thread = ei >= 1 && !(lane >= 16 && ew == 3);
         uint32_t G = 0, H = 0;
         for (int tile = blockIdx.x; tile < a.ntiles && !*vfail; tile += gridDim.x) {
             int i0, j0, k0, nown;
@@ -491,7 +485,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                 if (!wait(&full[Gl % NS], (Gl / NS) & 1u)) { ok = false; break; }
                 float Ecur = reinterpret_cast<const float*>(stages + (Gl % NS) * TC_STAGE_BYTES +
                                                             TC_STAGE_E)[(xo + ei) + TC_BOXX * ej];
-                if (PREC == 3) Ecur *= ldexpf(1.f, (int)dcol[SPLIT ? 48 : 24]);
+                if (SCALED) Ecur *= ldexpf(1.f, (int)dcol[SPLIT ? 48 : 24]);
                 float y[24];
                 if (SPLIT) {
 #pragma unroll
@@ -501,24 +495,53 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
 #pragma unroll
                     for (int r = 0; r < 24; ++r) y[r] = s2 * dcol[r];
                 }
-                float4* zr = reinterpret_cast<float4*>(sZ + et * TC_ZSTRIDE);
+                // Node assembly through registers.  Lane = ei + 16 * (ej & 1);
+                // y[3 (a + 2b + 4c) + comp] is this element's contribution to
+                // its local node (a, b, c).
+                // x: node (ei, ej+b, c) = a=0 part here + a=1 part of element ei-1
+                float X[2][2][3];
 #pragma unroll
-                for (int n8 = 0; n8 < 8; ++n8)
-                    zr[2 * (n8 & 3) + (n8 >> 2)] = make_float4(y[3 * n8], y[3 * n8 + 1], y[3 * n8 + 2], 0.f);
-                named_bar(2, 128);
-                if (node_thread) {
-                    float s0 = carry0, s1 = carry1, s2 = carry2, n0 = 0.f, n1 = 0.f, n2 = 0.f;
+                for (int bb = 0; bb < 2; ++bb)
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int ex = nli - 1 + (e & 1), ey = nlj - 1 + (e >> 1);
-                        const int loc = (nli - ex) + 2 * (nlj - ey);
-                        const float4* zz = reinterpret_cast<const float4*>(sZ + (ex + TC_EX * ey) * TC_ZSTRIDE);
-                        const float4 lo4 = zz[2 * loc], hi4 = zz[2 * loc + 1];
-                        s0 += lo4.x; s1 += lo4.y; s2 += lo4.z;
-                        n0 += hi4.x; n1 += hi4.y; n2 += hi4.z;
+                    for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            const float left = __shfl_up_sync(0xffffffffu, y[3 * (1 + 2 * bb + 4 * cc) + k], 1, 16);
+                            X[bb][cc][k] = y[3 * (2 * bb + 4 * cc) + k] + (ei > 0 ? left : 0.f);
+                        }
+                // y: lower half-warp (element row 2w) finishes node row 2w+1 with
+                // the upper half's b = 0 parts; the upper half (row 2w+1)
+                // finishes node row 2w+2 with the next warp's lower b = 0 parts
+                const bool upper = lane >= 16;
+                float N[2][3];
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const float v = __shfl_down_sync(0xffffffffu, X[0][cc][k], 16);
+                        N[cc][k] = X[1][cc][k] + (upper ? 0.f : v);
                     }
-                    carry0 = n0; carry1 = n1; carry2 = n2;
-                    const int gi = i0 + nli - 1, gj = j0 + nlj - 1, gk = k0 - 1 + l;
+                if (!upper) {
+#pragma unroll
+                    for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) sZ[(ew * 16 + ei) * 6 + 3 * cc + k] = X[0][cc][k];
+                }
+                named_bar(2, 128);
+                if (upper && ew < 3) {
+#pragma unroll
+                    for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) N[cc][k] += sZ[((ew + 1) * 16 + ei) * 6 + 3 * cc + k];
+                }
+                // z: node layer l = carry (c = 1 halves of layer l-1) + c = 0 halves
+                const float s0 = carry0 + N[0][0], s1 = carry1 + N[0][1], s2 = carry2 + N[0][2];
+                carry0 = N[1][0];
+                carry1 = N[1][1];
+                carry2 = N[1][2];
+                const int nrow = 2 * ew + 1 + (upper ? 1 : 0);            // node row in the tile
+                if (node_thread) {
+                    const int gi = i0 + ei - 1, gj = j0 + nrow - 1, gk = k0 - 1 + l;
                     if (l >= 1 && gi < g.nx && gj < g.ny) {
                         const long long pidx = gi + (long long)a.px * (gj + (long long)g.ny * gk);
                         a.q[pidx] = s0;
@@ -528,7 +551,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                             const uint32_t Gm = Gb + l;
                             if (!wait(&conv[Gm % NS], (Gm / NS) & 1u)) ok = false;
                             const float* pn = (const float*)(stages + (Gm % NS) * TC_STAGE_BYTES + TC_STAGE_P) +
-                                              (xo + nli) + TC_BOXX * nlj;
+                                              (xo + ei) + TC_BOXX * nrow;
                             tdot = fmaf(pn[0], s0, fmaf(pn[TC_PLANE], s1, fmaf(pn[2 * TC_PLANE], s2, tdot)));
                         }
                     }
@@ -600,7 +623,7 @@ __global__ void k_soa_to_aos(const Grid g, int px, long long vol, const float* _
 // ------------------------------------------------------------------ host side
 template <int PREC, bool FUSED, bool SPLIT>
 static void set_attr_one() {
-    constexpr int NSL = (PREC == 2) ? 2 : 1;
+    constexpr int NSL = (PREC == 2 || PREC == 4) ? 2 : 1;
     cudaFuncSetAttribute(k_matvec_tc<PREC, FUSED, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          TcSmemWs<NSL, SPLIT ? 64 : 32>::BYTES);
 }
@@ -610,6 +633,7 @@ static void set_attr_prec() {
     set_attr_one<1, FUSED, SPLIT>();
     set_attr_one<2, FUSED, SPLIT>();
     set_attr_one<3, FUSED, SPLIT>();
+    set_attr_one<4, FUSED, SPLIT>();
 }
 
 void init_tc_attributes() {
@@ -715,8 +739,8 @@ bool prepare_tc_operands(to3d_ctx* c) {
 
 template <int PREC, bool FUSED, bool SPLIT>
 static void launch_one(to3d_ctx* c, cudaStream_t s, const TcArgs& a, const CUtensorMap& tp) {
-    constexpr int NSL = (PREC == 2) ? 2 : 1;
-    const int per_sm = 2;
+    constexpr int NSL = (PREC == 2 || PREC == 4) ? 2 : 1;
+    const int per_sm = TC_CTAS_PER_SM;
     const int grid = a.ntiles < c->tc_grid * per_sm ? a.ntiles : c->tc_grid * per_sm;
     k_matvec_tc<PREC, FUSED, SPLIT><<<grid, TC_ROLE_THREADS, TcSmemWs<NSL, SPLIT ? 64 : 32>::BYTES, s>>>(
         a, c->tm_r, tp, c->tm_d, c->tm_e);
@@ -727,6 +751,7 @@ template <bool FUSED, bool SPLIT>
 static void launch_prec(to3d_ctx* c, cudaStream_t s, const TcArgs& a, int prec, const CUtensorMap& tp) {
     if (prec == TO3D_BF16X2_DC) launch_one<2, FUSED, SPLIT>(c, s, a, tp);
     else if (prec == TO3D_FP16_DC) launch_one<3, FUSED, SPLIT>(c, s, a, tp);
+    else if (prec == TO3D_FP16X2_DC) launch_one<4, FUSED, SPLIT>(c, s, a, tp);
     else launch_one<1, FUSED, SPLIT>(c, s, a, tp);
 }
 
@@ -748,7 +773,7 @@ void launch_matvec_tc(to3d_ctx* c, cudaStream_t s, int prec, bool fused, int par
     a.c_lam = (float)c->kes.c_lam;
     a.c_mu = (float)c->kes.c_mu;
     const int nmma = c->tc_split ? 64 : 32;
-    a.Bglob = c->tcB + (prec == TO3D_FP16_DC ? nmma * 64 : 0);
+    a.Bglob = c->tcB + ((prec == TO3D_FP16_DC || prec == TO3D_FP16X2_DC) ? nmma * 64 : 0);
     a.E32 = c->E32;
     a.p_new = fused ? (parity ? c->p32b : c->p32a) : nullptr;
     a.q = c->q32;

@@ -27,8 +27,16 @@ __device__ __forceinline__ long long gtid() {
     return blockIdx.x * (long long)blockDim.x + threadIdx.x;
 }
 
+__global__ void k_ss_segment(SolverScalars* ss, double tol2, int maxit) {
+    ss->tol2 = tol2;
+    ss->it = 0;
+    ss->done = 0;
+    ss->maxit = maxit;
+}
+
 __global__ void k_ss_reset(SolverScalars* ss, double tol2, int maxit) {
     ss->rz = ss->rz_new = ss->pq = ss->rr = ss->alpha = ss->beta = 0.0;
+    ss->zcoef = 1.0;
     ss->tol2 = tol2;
     ss->it = 0;
     ss->done = 0;
@@ -159,6 +167,7 @@ __global__ void k_pcg32_init(const Grid g, int px, long long vol, const double* 
         ss->rz = out[0];
         ss->rr = out[1];
         ss->beta = 0.0;
+        ss->zcoef = 1.0;
         if (!isfinite(out[0]) || !isfinite(out[1])) {
             ss->status = TO3D_ENUMERIC;
             ss->done = 1;
@@ -226,6 +235,7 @@ __global__ void __launch_bounds__(256)
     if (grid_sum<2>(red, v, sh, out) && threadIdx.x == 0) {
         const double rzn = out[0];
         ss->beta = rzn / ss->rz;
+        ss->zcoef = 1.0;
         ss->rz = rzn;
         ss->rr = out[1];
         ss->it += 1;
@@ -236,6 +246,58 @@ __global__ void __launch_bounds__(256)
             ss->done = 1;
         } else if (ss->it >= ss->maxit) {
             ss->status = TO3D_ENOCONV;
+            ss->done = 1;
+        }
+    }
+}
+
+// Residual replacement ("reliable update") of the inner solve: the FP32
+// recurrence residual is replaced by the true FP64 residual r' (scaled),
+// the correction d restarts at 0 (u has absorbed it), and the last search
+// direction p is kept.  To keep r'^T p = 0 the next direction is built from
+// p - gamma z' with z' = M^-1 r' and gamma = r'^T p / r'^T z', i.e.
+//   p_new = (1 - beta gamma) z' + beta p,   beta = r'^T z' / rz_old,
+// which the fused matvec forms through the coefficient zcoef.
+__global__ void k_pcg32_replace(const Grid g, int px, long long vol, const double* __restrict__ r64,
+                                double scale, const float* __restrict__ dinv,
+                                const float* __restrict__ p, float* __restrict__ r32,
+                                float* __restrict__ d32, const Reducer red, SolverScalars* ss,
+                                double delta2, double target2) {
+    __shared__ double sh[96];
+    __shared__ double out[3];
+    double rzd = 0.0, rrd = 0.0, rpd = 0.0;
+    for (long long n = gtid(); n < g.nnode; n += gstride()) {
+        const long long pp = (n % g.nx) + (long long)px * (n / g.nx);
+        const float di = dinv[pp];
+        float rz = 0.f, rr = 0.f, rp = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float rv = (float)(r64[3 * n + c] * scale);
+            r32[c * vol + pp] = rv;
+            d32[c * vol + pp] = 0.f;
+            rz = fmaf(di * rv, rv, rz);
+            rr = fmaf(rv, rv, rr);
+            rp = fmaf(rv, p[c * vol + pp], rp);
+        }
+        rzd += rz;
+        rrd += rr;
+        rpd += rp;
+    }
+    double v[3] = {rzd, rrd, rpd};
+    if (grid_sum<3>(red, v, sh, out) && threadIdx.x == 0) {
+        const double rz = out[0], rr = out[1], rp = out[2];
+        const double beta = rz / ss->rz;
+        const double gamma = rz > 0.0 ? rp / rz : 0.0;
+        ss->beta = beta;
+        ss->zcoef = 1.0 - beta * gamma;
+        ss->rz = rz;
+        ss->rr = rr;
+        ss->done = 0;
+        ss->tol2 = fmax(delta2 * rr, target2);     // next replacement after a drop by delta
+        if (!isfinite(rz) || !isfinite(rr) || !isfinite(rp)) {
+            ss->status = TO3D_ENUMERIC;
+            ss->done = 1;
+        } else if (rr <= ss->tol2) {
             ss->done = 1;
         }
     }
@@ -305,6 +367,14 @@ void launch_pcg32_iter(to3d_ctx* c, cudaStream_t s, int prec, int parity, cudaEv
     c->launches++;
 }
 
+void launch_pcg32_replace(to3d_ctx* c, cudaStream_t s, const double* r64, double scale,
+                          const float* p_latest, double delta2, double target2) {
+    k_pcg32_replace<<<vec_blocks(c->g.nnode), PCG_THREADS, 0, s>>>(
+        c->g, c->px, c->vol, r64, scale, c->dinv32, p_latest, c->r32, c->d32, c->red, c->ss,
+        delta2, target2);
+    c->launches++;
+}
+
 void launch_axpy_d32(to3d_ctx* c, cudaStream_t s, double inv_scale) {
     k_axpy_d32<<<vec_blocks(c->g.nnode), PCG_THREADS, 0, s>>>(c->g, c->px, c->vol, c->u, c->d32,
                                                                inv_scale);
@@ -313,6 +383,11 @@ void launch_axpy_d32(to3d_ctx* c, cudaStream_t s, double inv_scale) {
 
 void launch_norm2(to3d_ctx* c, cudaStream_t s, const double* v, long long n, double* out) {
     k_norm2<<<vec_blocks(n), PCG_THREADS, 0, s>>>(n, v, c->red, out);
+    c->launches++;
+}
+
+void launch_ss_segment(to3d_ctx* c, cudaStream_t s, double tol2, int maxit) {
+    k_ss_segment<<<1, 1, 0, s>>>(c->ss, tol2, maxit);
     c->launches++;
 }
 

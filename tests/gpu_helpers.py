@@ -49,11 +49,17 @@ def emulate_lowp(prob, x, p32, prec):
         hi = bf16_round(pe)
         lo = bf16_round((pe - hi).astype(np.float32))
         pe = hi.astype(np.float64) + lo.astype(np.float64)
-    elif prec == 3:
+    elif prec in (3, 4):
         m = np.abs(pe).max(axis=1)
         _, ex = np.frexp(np.where(m > 0, m, 1.0))
-        s = np.ldexp(1.0, 11 - ex)[:, None]
-        pe = (pe * s).astype(np.float16).astype(np.float64) / s
+        s = np.ldexp(1.0, 11 - ex)[:, None].astype(np.float32)
+        v = (pe * s).astype(np.float32)
+        hi = v.astype(np.float16).astype(np.float32)
+        if prec == 4:
+            lo = (v - hi).astype(np.float16).astype(np.float32)
+            pe = (hi.astype(np.float64) + lo.astype(np.float64)) / s
+        else:
+            pe = hi.astype(np.float64) / s
     ye = (pe @ KE) * E[:, None]
     y = np.bincount(ed.ravel(), weights=ye.ravel(), minlength=p32.size)
     absb = (np.abs(q[ed].astype(np.float64)) @ np.abs(KE)) * E[:, None]

@@ -61,7 +61,8 @@ def test_matvec64_device_pointers():
 
 
 @pytest.mark.parametrize("nu", [0.3, 0.33])
-@pytest.mark.parametrize("prec,tol_exact", [(1, 2.0 ** -8), (2, 2.0 ** -16), (3, 2.0 ** -10)])
+@pytest.mark.parametrize("prec,tol_exact", [(1, 2.0 ** -8), (2, 2.0 ** -16), (3, 2.0 ** -10),
+                                             (4, 2.0 ** -20)])
 @pytest.mark.parametrize("dims", SIZES)
 def test_matvec_tensor_core(dims, prec, tol_exact, nu):
     # nu = 0.3 uses one combined integer B (3 A_lam + 2 A_mu); nu = 0.33 has
@@ -83,7 +84,7 @@ def test_matvec_tensor_core(dims, prec, tol_exact, nu):
     assert np.array_equal(y[fx].astype(np.float32), p32[fx])
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2, 3])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3, 4])
 def test_solve_matches_direct(precision):
     prob = random_problem(24, 8, 4, seed=11, partial_clamp=False)
     x = problems.random_density(prob.nel, 12, 0.1, 1.0)
