@@ -203,6 +203,28 @@ TO3D_API to3d_status to3d_oc_update(to3d_ctx* ctx, const double* x, const double
                            double* lambda, double* volume, int32_t* halvings,
                            int32_t on_device);
 
+/* ---- many independent problems ------------------------------------------ */
+
+typedef struct to3d_batch to3d_batch;
+
+/* Create `nprob` independent problems (each as for to3d_create; params[i],
+ * fixed[i], load[i], passive[i] (passive may be NULL, or hold NULL entries)).
+ * Every problem's OC iteration is captured once as a CUDA graph whose solver
+ * and bisection loops run on the device (conditional graph nodes); the
+ * tensor-core kernel's z-segment length is autotuned per grid shape.  Only
+ * the tensor-core defect-correction precisions are accepted (EINVAL for
+ * TO3D_F64).  `stream`: the caller's stream that each step is ordered on. */
+TO3D_API to3d_status to3d_batch_create(int32_t nprob, const to3d_params* params,
+                                       const uint8_t* const* fixed, const double* const* load,
+                                       const uint8_t* const* passive, void* stream,
+                                       to3d_batch** out);
+/* One OC iteration of every problem (the graphs run side by side on a pool
+ * of streams); info [nprob] may be NULL.  Returns the worst status. */
+TO3D_API to3d_status to3d_batch_step(to3d_batch* b, to3d_iter_info* info);
+TO3D_API to3d_status to3d_batch_get_density(to3d_batch* b, int32_t i, double* x, int32_t on_device);
+TO3D_API int32_t to3d_batch_size(const to3d_batch* b);
+TO3D_API void to3d_batch_destroy(to3d_batch* b);
+
 /* Same results as to3d_sensitivity, but the library allocates nothing, and
  * no context is needed.  The paper has no counterpart: this entry point
  * exists for callers that cannot let a library call cudaMalloc.  Examples are

@@ -86,6 +86,12 @@ _SIGS = {
     "to3d_oc_update": (I32, [VP, VP, VP, VP, DP, DP, C.POINTER(I32), I32]),
     "to3d_sensitivity_noalloc": (I32, [I32, I32, I32, C.c_double, C.c_double, C.c_double,
                                        C.c_double, VP, VP, VP, VP, DP, VP]),
+    "to3d_batch_create": (I32, [I32, C.POINTER(Params), C.POINTER(VP), C.POINTER(VP),
+                                C.POINTER(VP), VP, C.POINTER(VP)]),
+    "to3d_batch_step": (I32, [VP, C.POINTER(IterInfo)]),
+    "to3d_batch_get_density": (I32, [VP, I32, VP, I32]),
+    "to3d_batch_size": (I32, [VP]),
+    "to3d_batch_destroy": (None, [VP]),
 }
 
 
@@ -318,3 +324,68 @@ def sensitivity_noalloc(nelx, nely, nelz, x, u, ce, dc, penal=3.0, E0=1.0, Emin=
     if st != 0:
         raise To3dError(st, "to3d_sensitivity_noalloc")
     return comp.value
+
+
+class Batch:
+    """Independent problems stepped together (``to3d_batch_*``)."""
+
+    def __init__(self, probs, stream=None, **params):
+        lib = load()
+        self.lib = lib
+        n = len(probs)
+        self.params = (Params * n)()
+        keep = []
+        fixed = (VP * n)()
+        loads = (VP * n)()
+        pas = (VP * n)()
+        for i, pr in enumerate(probs):
+            kw = dict(volfrac=pr.volfrac, penal=pr.penal, rmin=pr.rmin, E0=pr.E0, Emin=pr.Emin,
+                      nu=pr.nu, move=pr.move, bisect_tol=pr.bisect_tol, precision=BF16X2_DC)
+            kw.update(params)
+            self.params[i] = default_params(nelx=pr.nelx, nely=pr.nely, nelz=pr.nelz, **kw)
+            f = np.ascontiguousarray(pr.fixed, np.uint8)
+            l = np.ascontiguousarray(pr.load, np.float64)
+            keep += [f, l]
+            fixed[i], loads[i] = f.ctypes.data, l.ctypes.data
+            if pr.passive is not None:
+                pp = np.ascontiguousarray(pr.passive, np.uint8)
+                keep.append(pp)
+                pas[i] = pp.ctypes.data
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = 0
+        h = VP()
+        st = lib.to3d_batch_create(n, self.params, fixed, loads, pas, VP(stream), C.byref(h))
+        if st != 0:
+            raise To3dError(st, "to3d_batch_create failed")
+        self.h, self.n = h, n
+        self.nel = [pr.nel for pr in probs]
+
+    def step(self):
+        info = (IterInfo * self.n)()
+        st = self.lib.to3d_batch_step(self.h, info)
+        recs = [info[i].as_dict() for i in range(self.n)]
+        if st != 0:
+            raise To3dError(st, "to3d_batch_step")
+        return recs
+
+    def density(self, i):
+        out = np.empty(self.nel[i])
+        st = self.lib.to3d_batch_get_density(self.h, i, out.ctypes.data, 0)
+        if st != 0:
+            raise To3dError(st, "to3d_batch_get_density")
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.to3d_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

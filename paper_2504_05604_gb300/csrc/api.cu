@@ -168,6 +168,11 @@ static void free_all(to3d_ctx* c) {
             if (e) cudaEventDestroy(e);
     if (c->g_pcg64) cudaGraphExecDestroy(c->g_pcg64);
     if (c->g_pcg32) cudaGraphExecDestroy(c->g_pcg32);
+    if (c->g_iter) cudaGraphExecDestroy(c->g_iter);
+    if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
+    if (c->cap_stream3) cudaStreamDestroy(c->cap_stream3);
+    if (c->dcctl) cudaFree(c->dcctl);
+    if (c->dcctl_h) cudaFreeHost(c->dcctl_h);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c->st;
 }
@@ -262,6 +267,11 @@ static to3d_status pcg32_chunk(to3d_ctx* c, int prec, int n) {
     if (n == c->chunk) {
         if (!c->g_pcg32 || c->g_pcg32_prec != prec) {
             if (c->g_pcg32) cudaGraphExecDestroy(c->g_pcg32);
+    if (c->g_iter) cudaGraphExecDestroy(c->g_iter);
+    if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
+    if (c->cap_stream3) cudaStreamDestroy(c->cap_stream3);
+    if (c->dcctl) cudaFree(c->dcctl);
+    if (c->dcctl_h) cudaFreeHost(c->dcctl_h);
             c->g_pcg32 = nullptr;
             cudaGraph_t gr;
             CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));

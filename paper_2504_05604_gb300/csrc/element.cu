@@ -160,8 +160,13 @@ __global__ void k_oc_prep(long long nel, const double* __restrict__ x,
 template <int LEV>
 __global__ void __launch_bounds__(EL_THREADS)
     k_oc_pass(long long nel, const double* __restrict__ q, const double* __restrict__ lo,
-              const double* __restrict__ hi, const Reducer red, OCScalars* os) {
-    if (os->done) return;
+              const double* __restrict__ hi, const Reducer red, OCScalars* os,
+              cudaGraphConditionalHandle loop, int use_loop) {
+    if (os->done) {
+        // inside a graph loop the body must always decide the loop condition
+        if (use_loop && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(loop, 0u);
+        return;
+    }
     constexpr int NC = (1 << LEV) - 1;
     __shared__ double sh[32 * NC];
     __shared__ double out[NC];
@@ -205,6 +210,7 @@ __global__ void __launch_bounds__(EL_THREADS)
         }
         if (!os->done && !((os->l2 - os->l1) / (os->l1 + os->l2) > os->tol)) os->done = 1;
         if (!os->done) oc_build_tree(os);
+        if (use_loop) cudaGraphSetConditional(loop, os->done ? 0u : 1u);
     }
 }
 
@@ -279,15 +285,16 @@ void launch_oc_begin(to3d_ctx* c, cudaStream_t s, const double* x, const double*
     c->launches += 2;
 }
 
-void launch_oc_passes(to3d_ctx* c, cudaStream_t s, int npass) {
+void launch_oc_passes(to3d_ctx* c, cudaStream_t s, int npass, cudaGraphConditionalHandle loop,
+                      int use_loop) {
     const unsigned nb = el_blocks_capped(c->g.nel);
     for (int i = 0; i < npass; ++i) {
         switch (c->prm.oc_levels) {
-            case 1: k_oc_pass<1><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocq, c->oclo, c->ochi, c->red, c->os); break;
-            case 2: k_oc_pass<2><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocq, c->oclo, c->ochi, c->red, c->os); break;
-            case 3: k_oc_pass<3><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocq, c->oclo, c->ochi, c->red, c->os); break;
-            case 4: k_oc_pass<4><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocq, c->oclo, c->ochi, c->red, c->os); break;
-            default: k_oc_pass<5><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocq, c->oclo, c->ochi, c->red, c->os); break;
+            case 1: k_oc_pass<1><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocq, c->oclo, c->ochi, c->red, c->os, loop, use_loop); break;
+            case 2: k_oc_pass<2><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocq, c->oclo, c->ochi, c->red, c->os, loop, use_loop); break;
+            case 3: k_oc_pass<3><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocq, c->oclo, c->ochi, c->red, c->os, loop, use_loop); break;
+            case 4: k_oc_pass<4><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocq, c->oclo, c->ochi, c->red, c->os, loop, use_loop); break;
+            default: k_oc_pass<5><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocq, c->oclo, c->ochi, c->red, c->os, loop, use_loop); break;
         }
         c->launches++;
     }

@@ -145,6 +145,10 @@ struct to3d_ctx {
     cudaGraphExec_t g_pcg32 = nullptr;    // chunk of inner FP32 PCG iterations
     int g_pcg32_prec = -1;
     int chunk = 32;
+    cudaGraphExec_t g_iter = nullptr;     // whole OC iteration with device-side loops
+    cudaStream_t cap_stream2 = nullptr, cap_stream3 = nullptr;   // nested loop-body captures
+    void* dcctl = nullptr;                // device control block of the graph's solver
+    void* dcctl_h = nullptr;              // pinned copy of it
 };
 
 // ---------------------------------------------------------------- launchers
@@ -201,7 +205,8 @@ void launch_filter(to3d_ctx* c, cudaStream_t s, int mode, const double* a, const
                    double* out);
 void launch_oc_begin(to3d_ctx* c, cudaStream_t s, const double* x, const double* dcf,
                      double target);
-void launch_oc_passes(to3d_ctx* c, cudaStream_t s, int npass);
+void launch_oc_passes(to3d_ctx* c, cudaStream_t s, int npass,
+                      cudaGraphConditionalHandle loop = 0, int use_loop = 0);
 void launch_oc_apply(to3d_ctx* c, cudaStream_t s, const double* x, double* xnew);
 
 }  // namespace to3d
