@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", type=int, default=2, help="0 fp64, 1 bf16, 2 bf16x2, 3 fp16")
     ap.add_argument("--size", default="480x160x80")
+    ap.add_argument("--workload", default="large", choices=["large", "batched64"],
+                    help="large: the 480x160x80 cantilever; batched64: 64 seeded uneven "
+                         "cantilevers stepped together (extra measurement)")
     ap.add_argument("--inner-rtol", type=float, default=0.3,
                     help="residual-replacement factor of the defect-correction forms")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison step")
@@ -355,8 +358,57 @@ def ours(args):
         dist.destroy_process_group()
 
 
+def batched(args):
+    """64 seeded uneven cantilevers (0-3 spherical voids) stepped together,
+    one CUDA graph per problem and OC iteration; compared with stepping the
+    same problems one after another through single contexts."""
+    import torch
+    from paper_2504_05604_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2504_05604_gb300 import Batch, Context
+    from synth import problems
+
+    probs = problems.config_batched(64)
+    prec = args.precision if args.precision != 0 else 2
+    stream = torch.cuda.current_stream()
+    b = Batch(probs, precision=prec, inner_rtol=args.inner_rtol)
+    for _ in range(args.warmup):
+        b.step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    recs = [b.step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    b.close()
+    # the same problems one at a time (host-driven solver), one OC iteration each
+    t0 = time.perf_counter()
+    for pr in probs:
+        c = Context.from_problem(pr, precision=prec, inner_rtol=args.inner_rtol)
+        for _ in range(args.warmup):
+            c.step()
+        c.close()
+    torch.cuda.synchronize()
+    t_seq_warm = time.perf_counter() - t0
+    nel = sum(p.nel for p in probs)
+    print(json.dumps({
+        "metric": "OC iters/s, 64 seeded uneven cantilevers stepped together",
+        "value": 64 * args.steps / (ms / 1000.0), "unit": "problem OC iters/s",
+        "elements": nel, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "form": PREC_NAMES[prec], "status": max(r["status"] for rr in recs for r in rr),
+        "cg_iters_mean": statistics.mean(r["cg_iters"] for rr in recs for r in rr),
+        "sequential_single_contexts": {"value": 64 * args.warmup / t_seq_warm,
+                                       "unit": "problem OC iters/s",
+                                       "note": "first OC iterations, one problem after another"},
+    }))
+
+
 def main():
     args = parse()
+    if args.workload == "batched64" and not args.cpu_leg and args.impl == "ours":
+        batched(args)
+        return
     if args.cpu_leg:
         print(json.dumps(cpu_leg(args)))
         return
