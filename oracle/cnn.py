@@ -12,7 +12,14 @@ here; weights are [C_out, C_in, 3, 3, 3].
 
 Parity: pinned by tests/test_oracle_cnn.py (direct-loop convolution,
 identity and shift kernels, finite-difference gradients of every layer
-and of the whole network).
+and of the whole network, brute-force node densities, and hand-built
+pass-through networks that return the residual and the log density
+exactly, which pins the input scaling, channel order, padding and output
+mapping).
+
+The preconditioner is not part of the paper (whose solver is plain PCG,
+Section 2.3); this file defines what the library's learned preconditioner
+computes so that its kernels can be checked.
 """
 from __future__ import annotations
 
@@ -160,3 +167,74 @@ def relative_loss(out, target):
     d = out - target
     t2 = float(np.sum(target * target))
     return float(np.sum(d * d)) / t2, 2.0 * d / t2
+
+
+# ------------------------------------------------- the network as preconditioner
+
+
+def node_density(x, nelx, nely, nelz):
+    """Mean density of the elements sharing each node, node grid [nz, ny, nx].
+
+    Elements are numbered e = i + nelx (j + nely k), nodes on the
+    (nelx+1) x (nely+1) x (nelz+1) grid.
+    """
+    xe = np.asarray(x, dtype=np.float64).reshape(nelz, nely, nelx)
+    s = np.zeros((nelz + 1, nely + 1, nelx + 1))
+    cnt = np.zeros_like(s)
+    for c in (0, 1):
+        for b in (0, 1):
+            for a in (0, 1):
+                s[c:c + nelz, b:b + nely, a:a + nelx] += xe
+                cnt[c:c + nelz, b:b + nely, a:a + nelx] += 1.0
+    return s / cnt
+
+
+def padded_node_shape(nelx, nely, nelz):
+    """Node grid rounded up to multiples of 8 (three pooling levels)."""
+    return tuple((n + 1 + 7) // 8 * 8 for n in (nelz, nely, nelx))
+
+
+def preconditioner_input(r, x, fixed, nelx, nely, nelz):
+    """Network input [4, Zp, Yp, Xp] and the scale s = RMS(r) over all 3N dofs.
+
+    Channels 0..2: the residual's x, y, z components divided by s, zero on
+    clamped dofs; channel 3: log10(max(1e-3, node density)).  Zero outside
+    the node grid.
+    """
+    nx, ny, nz = nelx + 1, nely + 1, nelz + 1
+    r = np.where(np.asarray(fixed) != 0, 0.0, np.asarray(r, dtype=np.float64))
+    s = float(np.sqrt(np.sum(r * r) / r.size))
+    Zp, Yp, Xp = padded_node_shape(nelx, nely, nelz)
+    inp = np.zeros((IN_CH, Zp, Yp, Xp))
+    rn = (r / s if s > 0 else r).reshape(nz, ny, nx, 3)
+    for c in range(3):
+        inp[c, :nz, :ny, :nx] = rn[..., c]
+    inp[3, :nz, :ny, :nx] = np.log10(np.maximum(1e-3, node_density(x, nelx, nely, nelz)))
+    return inp, s
+
+
+def apply_preconditioner(params, r, x, fixed, nelx, nely, nelz):
+    """z = s * Net(input) on the node grid, zero on clamped dofs (dof d = 3n + c)."""
+    inp, s = preconditioner_input(r, x, fixed, nelx, nely, nelz)
+    out, _ = forward(params, inp)
+    nx, ny, nz = nelx + 1, nely + 1, nelz + 1
+    z = np.stack([out[c, :nz, :ny, :nx] for c in range(OUT_CH)], axis=-1).reshape(-1) * s
+    return np.where(np.asarray(fixed) != 0, 0.0, z)
+
+
+def preconditioner_loss(params, r, e, x, fixed, nelx, nely, nelz):
+    """Training loss of one sample and its parameter gradients.
+
+    The target is the error e = K^-1 r in the same normalised variables,
+    e / s, on the padded grid; the loss is ``relative_loss``.
+    """
+    inp, s = preconditioner_input(r, x, fixed, nelx, nely, nelz)
+    nx, ny, nz = nelx + 1, nely + 1, nelz + 1
+    tgt = np.zeros((OUT_CH,) + inp.shape[1:])
+    en = (np.asarray(e, dtype=np.float64) / s).reshape(nz, ny, nx, 3)
+    for c in range(OUT_CH):
+        tgt[c, :nz, :ny, :nx] = en[..., c]
+    out, cache = forward(params, inp)
+    L, gout = relative_loss(out, tgt)
+    grads, _ = backward(params, cache, gout)
+    return L, grads

@@ -103,3 +103,106 @@ def test_network_gradient_finite_differences():
         pm[key][idx] -= h
         fd = (loss(pp) - loss(pm)) / (2 * h)
         assert fd == pytest.approx(grads[key][idx], rel=1e-5, abs=1e-9), key
+
+
+def _zero_params(ch=cnn.CHANNELS):
+    return {k: np.zeros_like(v) for k, v in cnn.init_params(0, ch=ch).items()}
+
+
+def _pass_through(params, pick):
+    """Hand-built network whose output channel c is input channel pick[c].
+
+    ReLU layers carry a signed value v as the pair (relu(v), relu(-v)): the
+    first layer writes +v and -v, the level-0 layers copy the pairs (through
+    the skip connection, the deeper levels stay zero) and the output layer
+    forms relu(v) - relu(-v) = v.
+    """
+    c1 = params["e1a.w"].shape[0]
+    for c in range(cnn.IN_CH):
+        params["e0a.w"][2 * c, c, 1, 1, 1] = 1.0
+        params["e0a.w"][2 * c + 1, c, 1, 1, 1] = -1.0
+    for k in range(2 * cnn.IN_CH):
+        params["e0b.w"][k, k, 1, 1, 1] = 1.0
+        params["d0a.w"][k, c1 + k, 1, 1, 1] = 1.0
+        params["d0b.w"][k, k, 1, 1, 1] = 1.0
+    for o, c in enumerate(pick):
+        params["out.w"][o, 2 * c, 1, 1, 1] = 1.0
+        params["out.w"][o, 2 * c + 1, 1, 1, 1] = -1.0
+    return params
+
+
+def _small_problem(seed, nelx=5, nely=3, nelz=2):
+    r = rng(seed)
+    n = 3 * (nelx + 1) * (nely + 1) * (nelz + 1)
+    fixed = np.zeros(n, np.uint8)
+    fixed[: 3 * (nely + 1) * (nelz + 1) : 1] = 0
+    fixed[0:3] = 1                         # node 0 clamped
+    fixed[3 * 7 + 1] = 1                   # one more dof
+    x = r.uniform(1e-4, 1.0, nelx * nely * nelz)
+    return nelx, nely, nelz, x, r.standard_normal(n), fixed
+
+
+def test_node_density_brute_force():
+    nelx, nely, nelz = 3, 2, 2
+    x = rng(7).uniform(0, 1, nelx * nely * nelz)
+    d = cnn.node_density(x, nelx, nely, nelz)
+    for k in range(nelz + 1):
+        for j in range(nely + 1):
+            for i in range(nelx + 1):
+                vals = [x[ei + nelx * (ej + nely * ek)]
+                        for ek in (k - 1, k) for ej in (j - 1, j) for ei in (i - 1, i)
+                        if 0 <= ei < nelx and 0 <= ej < nely and 0 <= ek < nelz]
+                assert d[k, j, i] == pytest.approx(sum(vals) / len(vals), rel=1e-14)
+
+
+def test_pass_through_network_returns_residual():
+    nelx, nely, nelz, x, res, fixed = _small_problem(8)
+    params = _pass_through(_zero_params(), pick=(0, 1, 2))
+    z = cnn.apply_preconditioner(params, res, x, fixed, nelx, nely, nelz)
+    assert np.allclose(z, np.where(fixed != 0, 0.0, res), rtol=1e-13, atol=1e-14)
+    # error equal to the residual: zero loss
+    L, _ = cnn.preconditioner_loss(params, res, np.where(fixed != 0, 0.0, res), x, fixed,
+                                   nelx, nely, nelz)
+    assert L == pytest.approx(0.0, abs=1e-26)
+
+
+def test_pass_through_network_returns_log_density():
+    nelx, nely, nelz, x, res, fixed = _small_problem(9)
+    params = _pass_through(_zero_params(), pick=(3,))
+    z = cnn.apply_preconditioner(params, res, x, fixed, nelx, nely, nelz)
+    rm = np.where(fixed != 0, 0.0, res)
+    s = np.sqrt(np.mean(rm * rm))
+    ld = np.log10(np.maximum(1e-3, cnn.node_density(x, nelx, nely, nelz))).reshape(-1)
+    assert np.allclose(z[0::3], np.where(fixed[0::3] != 0, 0.0, s * ld), rtol=1e-13)
+    # output channels 1 and 2 have no weights: a bias comes out times s
+    params["out.b"][:] = [1.0, 2.0, 3.0]
+    z = cnn.apply_preconditioner(params, res, x, fixed, nelx, nely, nelz)
+    assert np.allclose(z[1::3], np.where(fixed[1::3] != 0, 0.0, s * 2.0), rtol=1e-13)
+
+
+def test_preconditioner_is_positively_homogeneous():
+    nelx, nely, nelz, x, res, fixed = _small_problem(10)
+    params = cnn.init_params(11, ch=(4, 4, 4, 4))
+    for k in params:
+        if k.endswith(".b"):
+            params[k] = 0.05 * rng(12).standard_normal(params[k].shape)
+    z1 = cnn.apply_preconditioner(params, res, x, fixed, nelx, nely, nelz)
+    z2 = cnn.apply_preconditioner(params, 3.7 * res, x, fixed, nelx, nely, nelz)
+    assert np.allclose(z2, 3.7 * z1, rtol=1e-12, atol=1e-300)
+    assert np.all(z1[fixed != 0] == 0.0) and np.any(z1 != 0.0)
+
+
+def test_preconditioner_loss_gradient_finite_differences():
+    nelx, nely, nelz, x, res, fixed = _small_problem(13)
+    params = cnn.init_params(14, ch=(2, 3, 3, 2))
+    e = rng(15).standard_normal(res.size)
+    L, grads = cnn.preconditioner_loss(params, res, e, x, fixed, nelx, nely, nelz)
+    h = 1e-6
+    for key, idx in [("e0a.w", (1, 3, 1, 1, 0)), ("d0a.w", (1, 4, 2, 1, 1)), ("out.b", (2,))]:
+        pp = {k: v.copy() for k, v in params.items()}
+        pm = {k: v.copy() for k, v in params.items()}
+        pp[key][idx] += h
+        pm[key][idx] -= h
+        fd = (cnn.preconditioner_loss(pp, res, e, x, fixed, nelx, nely, nelz)[0] -
+              cnn.preconditioner_loss(pm, res, e, x, fixed, nelx, nely, nelz)[0]) / (2 * h)
+        assert fd == pytest.approx(grads[key][idx], rel=1e-5, abs=1e-10), key
