@@ -15,7 +15,7 @@ identity and shift kernels, finite-difference gradients of every layer
 and of the whole network, brute-force node densities, and hand-built
 pass-through networks that return the residual and the log density
 exactly, which pins the input scaling, channel order, padding and output
-mapping).
+mapping; the energy-norm loss against a dense Cholesky factor).
 
 The preconditioner is not part of the paper (whose solver is plain PCG,
 Section 2.3); this file defines what the library's learned preconditioner
@@ -222,19 +222,28 @@ def apply_preconditioner(params, r, x, fixed, nelx, nely, nelz):
     return np.where(np.asarray(fixed) != 0, 0.0, z)
 
 
-def preconditioner_loss(params, r, e, x, fixed, nelx, nely, nelz):
-    """Training loss of one sample and its parameter gradients.
+def preconditioner_loss(params, r, e, x, fixed, nelx, nely, nelz, K):
+    """Training loss of one sample in the energy norm, and its gradients.
 
-    The target is the error e = K^-1 r in the same normalised variables,
-    e / s, on the padded grid; the loss is ``relative_loss``.
+    With z = M(r) (``apply_preconditioner``) and e = K^-1 r the exact
+    correction, L = ||z - e||_K^2 / ||e||_K^2 = (z^T K z - 2 z^T r + r^T e) /
+    (r^T e), K the clamped operator.  L < 1 implies r^T z > z^T K z / 2 > 0:
+    a network that beats z = 0 on a residual is a descent direction for it.
+    Returns (L, grads) with dL/dz = 2 (K z - r) / (r^T e) carried back
+    through the output scaling (times s) and the network.
     """
     inp, s = preconditioner_input(r, x, fixed, nelx, nely, nelz)
     nx, ny, nz = nelx + 1, nely + 1, nelz + 1
-    tgt = np.zeros((OUT_CH,) + inp.shape[1:])
-    en = (np.asarray(e, dtype=np.float64) / s).reshape(nz, ny, nx, 3)
-    for c in range(OUT_CH):
-        tgt[c, :nz, :ny, :nx] = en[..., c]
+    free = np.asarray(fixed) == 0
+    r = np.where(free, np.asarray(r, dtype=np.float64), 0.0)
     out, cache = forward(params, inp)
-    L, gout = relative_loss(out, tgt)
+    z = np.where(free, np.stack([out[c, :nz, :ny, :nx] for c in range(OUT_CH)],
+                                axis=-1).reshape(-1) * s, 0.0)
+    q = K @ z
+    rte = float(np.dot(r, e))
+    L = (float(np.dot(z, q)) - 2.0 * float(np.dot(z, r)) + rte) / rte
+    gz = np.where(free, 2.0 * (q - r) / rte, 0.0)
+    gout = np.zeros_like(out)
+    gout[:, :nz, :ny, :nx] = (s * gz).reshape(nz, ny, nx, 3).transpose(3, 0, 1, 2)
     grads, _ = backward(params, cache, gout)
     return L, grads

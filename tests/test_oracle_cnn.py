@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from oracle import cnn
+from oracle import cnn, fem
 
 
 def rng(seed):
@@ -135,8 +135,9 @@ def _small_problem(seed, nelx=5, nely=3, nelz=2):
     r = rng(seed)
     n = 3 * (nelx + 1) * (nely + 1) * (nelz + 1)
     fixed = np.zeros(n, np.uint8)
-    fixed[: 3 * (nely + 1) * (nelz + 1) : 1] = 0
-    fixed[0:3] = 1                         # node 0 clamped
+    face = (nelx + 1) * np.arange((nely + 1) * (nelz + 1))       # nodes with i = 0
+    for c in range(3):
+        fixed[3 * face + c] = 1            # clamped x = 0 face
     fixed[3 * 7 + 1] = 1                   # one more dof
     x = r.uniform(1e-4, 1.0, nelx * nely * nelz)
     return nelx, nely, nelz, x, r.standard_normal(n), fixed
@@ -160,10 +161,6 @@ def test_pass_through_network_returns_residual():
     params = _pass_through(_zero_params(), pick=(0, 1, 2))
     z = cnn.apply_preconditioner(params, res, x, fixed, nelx, nely, nelz)
     assert np.allclose(z, np.where(fixed != 0, 0.0, res), rtol=1e-13, atol=1e-14)
-    # error equal to the residual: zero loss
-    L, _ = cnn.preconditioner_loss(params, res, np.where(fixed != 0, 0.0, res), x, fixed,
-                                   nelx, nely, nelz)
-    assert L == pytest.approx(0.0, abs=1e-26)
 
 
 def test_pass_through_network_returns_log_density():
@@ -192,17 +189,44 @@ def test_preconditioner_is_positively_homogeneous():
     assert np.all(z1[fixed != 0] == 0.0) and np.any(z1 != 0.0)
 
 
+def _operator(nelx, nely, nelz, x, fixed):
+    KE = fem.element_stiffness(0.3)
+    return fem.apply_bc(fem.assemble(nelx, nely, nelz, fem.simp_modulus(x, 3.0), KE), fixed)
+
+
+def test_energy_loss_against_cholesky():
+    """L = ||z - e||_K^2 / ||e||_K^2 through a dense Cholesky factor of the
+    free block (K_ff = C C^T, ||v||_K = ||C^T v||), for a zero network (L = 1
+    exactly), a pass-through network (z = r) and a random one."""
+    nelx, nely, nelz, x, res, fixed = _small_problem(16)
+    K = _operator(nelx, nely, nelz, x, fixed)
+    free = np.flatnonzero(fixed == 0)
+    Ch = np.linalg.cholesky(K.toarray()[np.ix_(free, free)])
+    r = np.where(fixed != 0, 0.0, res)
+    e = fem.solve_dense(K, r, fixed)
+    knorm2 = lambda v: float(np.sum((Ch.T @ v[free]) ** 2))
+    L, _ = cnn.preconditioner_loss(_zero_params(), r, e, x, fixed, nelx, nely, nelz, K)
+    assert L == pytest.approx(1.0, rel=1e-12)
+    for params in (_pass_through(_zero_params(), pick=(0, 1, 2)), cnn.init_params(17)):
+        z = cnn.apply_preconditioner(params, r, x, fixed, nelx, nely, nelz)
+        L, _ = cnn.preconditioner_loss(params, r, e, x, fixed, nelx, nely, nelz, K)
+        assert L == pytest.approx(knorm2(z - e) / knorm2(e), rel=1e-9)
+
+
 def test_preconditioner_loss_gradient_finite_differences():
     nelx, nely, nelz, x, res, fixed = _small_problem(13)
+    K = _operator(nelx, nely, nelz, x, fixed)
+    r = np.where(fixed != 0, 0.0, res)
+    e = fem.solve_dense(K, r, fixed)
     params = cnn.init_params(14, ch=(2, 3, 3, 2))
-    e = rng(15).standard_normal(res.size)
-    L, grads = cnn.preconditioner_loss(params, res, e, x, fixed, nelx, nely, nelz)
+    L, grads = cnn.preconditioner_loss(params, r, e, x, fixed, nelx, nely, nelz, K)
     h = 1e-6
-    for key, idx in [("e0a.w", (1, 3, 1, 1, 0)), ("d0a.w", (1, 4, 2, 1, 1)), ("out.b", (2,))]:
+    for key, idx in [("e0a.w", (1, 3, 1, 1, 0)), ("d0a.w", (1, 4, 2, 1, 1)), ("out.b", (2,)),
+                     ("e2b.w", (1, 2, 0, 1, 2))]:
         pp = {k: v.copy() for k, v in params.items()}
         pm = {k: v.copy() for k, v in params.items()}
         pp[key][idx] += h
         pm[key][idx] -= h
-        fd = (cnn.preconditioner_loss(pp, res, e, x, fixed, nelx, nely, nelz)[0] -
-              cnn.preconditioner_loss(pm, res, e, x, fixed, nelx, nely, nelz)[0]) / (2 * h)
+        fd = (cnn.preconditioner_loss(pp, r, e, x, fixed, nelx, nely, nelz, K)[0] -
+              cnn.preconditioner_loss(pm, r, e, x, fixed, nelx, nely, nelz, K)[0]) / (2 * h)
         assert fd == pytest.approx(grads[key][idx], rel=1e-5, abs=1e-10), key
