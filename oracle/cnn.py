@@ -5,9 +5,10 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 The learned preconditioner is a small U-Net on the node grid: four levels
 with 16/32/64/64 channels, 3x3x3 convolutions with zero "same" padding,
 2x2x2 average pooling down, nearest-neighbour x2 up with skip
-concatenation, ReLU.  Input: the three residual components divided by
-their RMS and log10 of the node density; output: three correction
-components (times the same RMS).  Tensors are channels-first [C, Z, Y, X]
+concatenation, ReLU.  Input: the three components of the Jacobi-scaled
+residual D^-1/2 r divided by their RMS, and log10 of the node density;
+output: three components of a correction added to Jacobi, z = D^-1 r +
+RMS * D^-1/2 Net(...).  Tensors are channels-first [C, Z, Y, X]
 here; weights are [C_out, C_in, 3, 3, 3].
 
 Parity: pinned by tests/test_oracle_cnn.py (direct-loop convolution,
@@ -194,56 +195,67 @@ def padded_node_shape(nelx, nely, nelz):
     return tuple((n + 1 + 7) // 8 * 8 for n in (nelz, nely, nelx))
 
 
-def preconditioner_input(r, x, fixed, nelx, nely, nelz):
-    """Network input [4, Zp, Yp, Xp] and the scale s = RMS(r) over all 3N dofs.
+def preconditioner_input(r, x, fixed, dinv, nelx, nely, nelz):
+    """Network input [4, Zp, Yp, Xp] and the scale s.
 
-    Channels 0..2: the residual's x, y, z components divided by s, zero on
-    clamped dofs; channel 3: log10(max(1e-3, node density)).  Zero outside
-    the node grid.
+    The residual enters Jacobi-scaled, rt = D^-1/2 r (dinv = 1/diag(K) per
+    dof, clamped entries zero), which takes the 1e9 stiffness contrast of
+    SIMP out of what the network sees; s = RMS(rt) over all 3N dofs.
+    Channels 0..2: the x, y, z components of rt / s; channel 3:
+    log10(max(1e-3, node density)).  Zero outside the node grid.
     """
     nx, ny, nz = nelx + 1, nely + 1, nelz + 1
-    r = np.where(np.asarray(fixed) != 0, 0.0, np.asarray(r, dtype=np.float64))
-    s = float(np.sqrt(np.sum(r * r) / r.size))
+    free = np.asarray(fixed) == 0
+    rt = np.where(free, np.sqrt(dinv) * np.asarray(r, dtype=np.float64), 0.0)
+    s = float(np.sqrt(np.sum(rt * rt) / rt.size))
     Zp, Yp, Xp = padded_node_shape(nelx, nely, nelz)
     inp = np.zeros((IN_CH, Zp, Yp, Xp))
-    rn = (r / s if s > 0 else r).reshape(nz, ny, nx, 3)
+    rn = (rt / s if s > 0 else rt).reshape(nz, ny, nx, 3)
     for c in range(3):
         inp[c, :nz, :ny, :nx] = rn[..., c]
     inp[3, :nz, :ny, :nx] = np.log10(np.maximum(1e-3, node_density(x, nelx, nely, nelz)))
     return inp, s
 
 
-def apply_preconditioner(params, r, x, fixed, nelx, nely, nelz):
-    """z = s * Net(input) on the node grid, zero on clamped dofs (dof d = 3n + c)."""
-    inp, s = preconditioner_input(r, x, fixed, nelx, nely, nelz)
-    out, _ = forward(params, inp)
+def _network_to_dofs(out, nelx, nely, nelz):
     nx, ny, nz = nelx + 1, nely + 1, nelz + 1
-    z = np.stack([out[c, :nz, :ny, :nx] for c in range(OUT_CH)], axis=-1).reshape(-1) * s
-    return np.where(np.asarray(fixed) != 0, 0.0, z)
+    return np.stack([out[c, :nz, :ny, :nx] for c in range(OUT_CH)], axis=-1).reshape(-1)
 
 
-def preconditioner_loss(params, r, e, x, fixed, nelx, nely, nelz, K):
+def apply_preconditioner(params, r, x, fixed, dinv, nelx, nely, nelz):
+    """z = D^-1 r + s D^-1/2 Net(input): Jacobi plus a learned correction in
+    the Jacobi-scaled variables; zero on clamped dofs (dof d = 3n + c).  A
+    zero network gives plain Jacobi."""
+    inp, s = preconditioner_input(r, x, fixed, dinv, nelx, nely, nelz)
+    out, _ = forward(params, inp)
+    free = np.asarray(fixed) == 0
+    z = dinv * np.asarray(r, dtype=np.float64) + s * np.sqrt(dinv) * _network_to_dofs(
+        out, nelx, nely, nelz)
+    return np.where(free, z, 0.0)
+
+
+def preconditioner_loss(params, r, e, x, fixed, dinv, nelx, nely, nelz, K):
     """Training loss of one sample in the energy norm, and its gradients.
 
     With z = M(r) (``apply_preconditioner``) and e = K^-1 r the exact
     correction, L = ||z - e||_K^2 / ||e||_K^2 = (z^T K z - 2 z^T r + r^T e) /
     (r^T e), K the clamped operator.  L < 1 implies r^T z > z^T K z / 2 > 0:
-    a network that beats z = 0 on a residual is a descent direction for it.
-    Returns (L, grads) with dL/dz = 2 (K z - r) / (r^T e) carried back
-    through the output scaling (times s) and the network.
+    a preconditioner that beats z = 0 on a residual is a descent direction
+    for it.  Returns (L, grads) with dL/dz = 2 (K z - r) / (r^T e) carried
+    back through the output scaling (s D^-1/2) and the network.
     """
-    inp, s = preconditioner_input(r, x, fixed, nelx, nely, nelz)
+    inp, s = preconditioner_input(r, x, fixed, dinv, nelx, nely, nelz)
     nx, ny, nz = nelx + 1, nely + 1, nelz + 1
     free = np.asarray(fixed) == 0
     r = np.where(free, np.asarray(r, dtype=np.float64), 0.0)
     out, cache = forward(params, inp)
-    z = np.where(free, np.stack([out[c, :nz, :ny, :nx] for c in range(OUT_CH)],
-                                axis=-1).reshape(-1) * s, 0.0)
+    z = np.where(free, dinv * r + s * np.sqrt(dinv) * _network_to_dofs(out, nelx, nely, nelz),
+                 0.0)
     q = K @ z
     rte = float(np.dot(r, e))
     L = (float(np.dot(z, q)) - 2.0 * float(np.dot(z, r)) + rte) / rte
     gz = np.where(free, 2.0 * (q - r) / rte, 0.0)
     gout = np.zeros_like(out)
-    gout[:, :nz, :ny, :nx] = (s * gz).reshape(nz, ny, nx, 3).transpose(3, 0, 1, 2)
+    gout[:, :nz, :ny, :nx] = (s * np.sqrt(dinv) * gz).reshape(nz, ny, nx, 3).transpose(3, 0, 1, 2)
     grads, _ = backward(params, cache, gout)
     return L, grads

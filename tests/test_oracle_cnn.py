@@ -131,6 +131,12 @@ def _pass_through(params, pick):
     return params
 
 
+def _dinv(nelx, nely, nelz, x, fixed):
+    KE = fem.element_stiffness(0.3)
+    d = fem.jacobi_diagonal(nelx, nely, nelz, fem.simp_modulus(x, 3.0), KE, fixed)
+    return np.where(fixed != 0, 0.0, 1.0 / d)
+
+
 def _small_problem(seed, nelx=5, nely=3, nelz=2):
     r = rng(seed)
     n = 3 * (nelx + 1) * (nely + 1) * (nelz + 1)
@@ -157,34 +163,42 @@ def test_node_density_brute_force():
 
 
 def test_pass_through_network_returns_residual():
+    """Output = the scaled input rt / s: z = D^-1 r + D^-1/2 rt = 2 D^-1 r."""
     nelx, nely, nelz, x, res, fixed = _small_problem(8)
+    dinv = _dinv(nelx, nely, nelz, x, fixed)
     params = _pass_through(_zero_params(), pick=(0, 1, 2))
-    z = cnn.apply_preconditioner(params, res, x, fixed, nelx, nely, nelz)
-    assert np.allclose(z, np.where(fixed != 0, 0.0, res), rtol=1e-13, atol=1e-14)
+    z = cnn.apply_preconditioner(params, res, x, fixed, dinv, nelx, nely, nelz)
+    assert np.allclose(z, np.where(fixed != 0, 0.0, 2.0 * dinv * res), rtol=1e-13, atol=1e-300)
+    z0 = cnn.apply_preconditioner(_zero_params(), res, x, fixed, dinv, nelx, nely, nelz)
+    assert np.allclose(z0, np.where(fixed != 0, 0.0, dinv * res), rtol=1e-14, atol=1e-300)
 
 
 def test_pass_through_network_returns_log_density():
     nelx, nely, nelz, x, res, fixed = _small_problem(9)
+    dinv = _dinv(nelx, nely, nelz, x, fixed)
     params = _pass_through(_zero_params(), pick=(3,))
-    z = cnn.apply_preconditioner(params, res, x, fixed, nelx, nely, nelz)
-    rm = np.where(fixed != 0, 0.0, res)
-    s = np.sqrt(np.mean(rm * rm))
+    z = cnn.apply_preconditioner(params, res, x, fixed, dinv, nelx, nely, nelz)
+    rt = np.where(fixed != 0, 0.0, np.sqrt(dinv) * res)
+    s = np.sqrt(np.mean(rt * rt))
     ld = np.log10(np.maximum(1e-3, cnn.node_density(x, nelx, nely, nelz))).reshape(-1)
-    assert np.allclose(z[0::3], np.where(fixed[0::3] != 0, 0.0, s * ld), rtol=1e-13)
-    # output channels 1 and 2 have no weights: a bias comes out times s
+    ref = dinv * res + s * np.sqrt(dinv) * np.repeat(ld, 3) * np.tile([1.0, 0.0, 0.0], ld.size)
+    assert np.allclose(z, np.where(fixed != 0, 0.0, ref), rtol=1e-13, atol=1e-300)
+    # output channels 1 and 2 have no weights: a bias comes out times s D^-1/2
     params["out.b"][:] = [1.0, 2.0, 3.0]
-    z = cnn.apply_preconditioner(params, res, x, fixed, nelx, nely, nelz)
-    assert np.allclose(z[1::3], np.where(fixed[1::3] != 0, 0.0, s * 2.0), rtol=1e-13)
+    z = cnn.apply_preconditioner(params, res, x, fixed, dinv, nelx, nely, nelz)
+    ref = dinv[1::3] * res[1::3] + s * np.sqrt(dinv[1::3]) * 2.0
+    assert np.allclose(z[1::3], np.where(fixed[1::3] != 0, 0.0, ref), rtol=1e-13)
 
 
 def test_preconditioner_is_positively_homogeneous():
     nelx, nely, nelz, x, res, fixed = _small_problem(10)
+    dinv = _dinv(nelx, nely, nelz, x, fixed)
     params = cnn.init_params(11, ch=(4, 4, 4, 4))
     for k in params:
         if k.endswith(".b"):
             params[k] = 0.05 * rng(12).standard_normal(params[k].shape)
-    z1 = cnn.apply_preconditioner(params, res, x, fixed, nelx, nely, nelz)
-    z2 = cnn.apply_preconditioner(params, 3.7 * res, x, fixed, nelx, nely, nelz)
+    z1 = cnn.apply_preconditioner(params, res, x, fixed, dinv, nelx, nely, nelz)
+    z2 = cnn.apply_preconditioner(params, 3.7 * res, x, fixed, dinv, nelx, nely, nelz)
     assert np.allclose(z2, 3.7 * z1, rtol=1e-12, atol=1e-300)
     assert np.all(z1[fixed != 0] == 0.0) and np.any(z1 != 0.0)
 
@@ -196,30 +210,31 @@ def _operator(nelx, nely, nelz, x, fixed):
 
 def test_energy_loss_against_cholesky():
     """L = ||z - e||_K^2 / ||e||_K^2 through a dense Cholesky factor of the
-    free block (K_ff = C C^T, ||v||_K = ||C^T v||), for a zero network (L = 1
-    exactly), a pass-through network (z = r) and a random one."""
+    free block (K_ff = C C^T, ||v||_K = ||C^T v||), for a zero network
+    (plain Jacobi), a pass-through network and a random one."""
     nelx, nely, nelz, x, res, fixed = _small_problem(16)
     K = _operator(nelx, nely, nelz, x, fixed)
+    dinv = _dinv(nelx, nely, nelz, x, fixed)
     free = np.flatnonzero(fixed == 0)
     Ch = np.linalg.cholesky(K.toarray()[np.ix_(free, free)])
     r = np.where(fixed != 0, 0.0, res)
     e = fem.solve_dense(K, r, fixed)
     knorm2 = lambda v: float(np.sum((Ch.T @ v[free]) ** 2))
-    L, _ = cnn.preconditioner_loss(_zero_params(), r, e, x, fixed, nelx, nely, nelz, K)
-    assert L == pytest.approx(1.0, rel=1e-12)
-    for params in (_pass_through(_zero_params(), pick=(0, 1, 2)), cnn.init_params(17)):
-        z = cnn.apply_preconditioner(params, r, x, fixed, nelx, nely, nelz)
-        L, _ = cnn.preconditioner_loss(params, r, e, x, fixed, nelx, nely, nelz, K)
+    for params in (_zero_params(), _pass_through(_zero_params(), pick=(0, 1, 2)),
+                   cnn.init_params(17)):
+        z = cnn.apply_preconditioner(params, r, x, fixed, dinv, nelx, nely, nelz)
+        L, _ = cnn.preconditioner_loss(params, r, e, x, fixed, dinv, nelx, nely, nelz, K)
         assert L == pytest.approx(knorm2(z - e) / knorm2(e), rel=1e-9)
 
 
 def test_preconditioner_loss_gradient_finite_differences():
     nelx, nely, nelz, x, res, fixed = _small_problem(13)
     K = _operator(nelx, nely, nelz, x, fixed)
+    dinv = _dinv(nelx, nely, nelz, x, fixed)
     r = np.where(fixed != 0, 0.0, res)
     e = fem.solve_dense(K, r, fixed)
     params = cnn.init_params(14, ch=(2, 3, 3, 2))
-    L, grads = cnn.preconditioner_loss(params, r, e, x, fixed, nelx, nely, nelz, K)
+    L, grads = cnn.preconditioner_loss(params, r, e, x, fixed, dinv, nelx, nely, nelz, K)
     h = 1e-6
     for key, idx in [("e0a.w", (1, 3, 1, 1, 0)), ("d0a.w", (1, 4, 2, 1, 1)), ("out.b", (2,)),
                      ("e2b.w", (1, 2, 0, 1, 2))]:
@@ -227,6 +242,6 @@ def test_preconditioner_loss_gradient_finite_differences():
         pm = {k: v.copy() for k, v in params.items()}
         pp[key][idx] += h
         pm[key][idx] -= h
-        fd = (cnn.preconditioner_loss(pp, r, e, x, fixed, nelx, nely, nelz, K)[0] -
-              cnn.preconditioner_loss(pm, r, e, x, fixed, nelx, nely, nelz, K)[0]) / (2 * h)
+        fd = (cnn.preconditioner_loss(pp, r, e, x, fixed, dinv, nelx, nely, nelz, K)[0] -
+              cnn.preconditioner_loss(pm, r, e, x, fixed, dinv, nelx, nely, nelz, K)[0]) / (2 * h)
         assert fd == pytest.approx(grads[key][idx], rel=1e-5, abs=1e-10), key
