@@ -203,6 +203,91 @@ TO3D_API to3d_status to3d_oc_update(to3d_ctx* ctx, const double* x, const double
                            double* lambda, double* volume, int32_t* halvings,
                            int32_t on_device);
 
+/* ---- learned preconditioner ----------------------------------------------
+ * Not in the paper, whose solver is plain PCG (Section 2.3, Table 2): an
+ * optional preconditioner for the same FP64 state equation.
+ * A four-level U-Net on the node grid (16/32/64/64 channels, 3x3x3
+ * convolutions with zero padding, 2x2x2 average pooling, nearest x2
+ * upsampling with skip concatenation, ReLU), applied as z = M(r) inside
+ * flexible CG when params.precond = TO3D_CNN_FCG.  Inputs: the Jacobi-scaled
+ * residual rt = D^-1/2 r (D = diag K) divided by s = RMS(rt), three
+ * channels, and log10 of the node density; output: a correction on top of
+ * Jacobi, z = D^-1 r + s D^-1/2 out (a zero network is plain Jacobi).
+ * Clamped dofs are zero in and out.  Parameters
+ * are FP32 (flat vector, per layer: weights [27][C_out][C_in] with tap =
+ * 9 dz + 3 dy + dx, then bias [C_out]); the convolutions run on the tensor
+ * cores in BF16 with FP32 accumulation.  Flexible CG (FP64 vectors,
+ * Polak-Ribiere beta, exact line search) takes z = D^-1 r (Jacobi) in any
+ * iteration where the network's r^T z <= 0, and falls back to Jacobi-PCG
+ * when a curvature p^T K p is non-positive, when the smallest residual seen
+ * drops by less than 10 % over 200 iterations, or when, past 50
+ * iterations, it is 10x above where the context's last plain Jacobi-PCG
+ * solve (its iteration count at the same tolerance) would have been at its
+ * average rate; to3d_solve_info.outer is then 2 (the fallback starts from
+ * zero unless the true residual is already below 1e-2 |f|).  The true FP64
+ * residual decides convergence. */
+
+/* (Re)initialise the network's parameters (He-normal, counter-based hash
+ * of `seed`); clears the optimiser state.  Network not trained afterwards. */
+TO3D_API to3d_status to3d_cnn_init(to3d_ctx* ctx, uint64_t seed);
+/* Number of FP32 parameters (allocates the network if needed). */
+TO3D_API to3d_status to3d_cnn_param_count(to3d_ctx* ctx, int64_t* n);
+/* Copy the parameters out (host buffer of n floats; EINVAL if n differs). */
+TO3D_API to3d_status to3d_cnn_get_params(to3d_ctx* ctx, float* p, int64_t n);
+/* Load parameters (host buffer of n floats); marks the network trained. */
+TO3D_API to3d_status to3d_cnn_set_params(to3d_ctx* ctx, const float* p, int64_t n);
+/* z = M(r) for densities x [nel] and residual r [3N]; z [3N].  EINVAL if
+ * the network does not exist yet (call to3d_cnn_init first). */
+TO3D_API to3d_status to3d_cnn_apply(to3d_ctx* ctx, const double* x, const double* r, double* z,
+                                    int32_t on_device);
+/* Train on the GPU.  Snapshots: `nsnap` residuals r = f - K u of FP64
+ * Jacobi-PCG (source 0) or of flexible CG with the current network
+ * (source 1: the residuals the network itself leaves) from u = 0 on the
+ * context's design, the first of every `per_design` taken before any
+ * iteration (r = f), the others after a random 1..200 iterations; each stores r, the design and r^T K^-1 r (FP64
+ * solve to 1e-10).  After every `per_design` snapshots the design advances
+ * by one plain OC iteration (FP64 Jacobi-PCG).  Then `steps` Adam steps
+ * (lr, betas 0.9 / 0.999), one snapshot per step, on the energy-norm loss
+ * L = ||M(r) - K^-1 r||_K^2 / ||K^-1 r||_K^2 = (z^T K z - 2 z^T r + r^T e) /
+ * (r^T e), z = M(r), e = K^-1 r (L < 1 implies r^T z > 0).  loss_first /
+ * loss_last (host, may be NULL): mean loss of the first and last tenth of
+ * the steps.  Snapshots stay resident and accumulate over calls (nsnap = 0
+ * trains on those already taken; steps = 0 only takes snapshots).
+ * Continues from the current parameters (initialised from `seed` if none
+ * were set).  The context's displacement is not kept (the next solve
+ * starts from zero). */
+TO3D_API to3d_status to3d_cnn_train(to3d_ctx* ctx, int32_t nsnap, int32_t per_design,
+                                    int32_t steps, double lr, uint64_t seed, int32_t source,
+                                    double* loss_first, double* loss_last);
+/* The training loss of one sample and its gradient with respect to every
+ * parameter (same layout as to3d_cnn_get_params), without an optimiser
+ * step: x [nel] densities, r [3N] residual (clamped entries ignored), e [3N]
+ * its error K^-1 r, needed only for r^T e > 0 (EINVAL otherwise), all as
+ * `on_device`; grad: host buffer of ngrad floats (NULL to skip); *loss on
+ * host. */
+TO3D_API to3d_status to3d_cnn_loss_grad(to3d_ctx* ctx, const double* x, const double* r,
+                                        const double* e, int32_t on_device, float* grad,
+                                        int64_t ngrad, double* loss);
+/* One 3x3x3 convolution on caller device buffers (channels-last, zero
+ * padding): out[v][Cout] (FP32) = bias + W * concat(in1[v][C1], in2[v][C2]),
+ * ReLU if relu.  in1, in2 BF16; W BF16 [27][Cout][C1+C2]; bias FP32 or NULL.
+ * C1 >= 16 and C2 >= 0 multiples of 16, Cout/8 in {1,2,4,6,8,12,16}.
+ * Enqueued on `stream` (cudaStream_t as void*), not synchronised. */
+TO3D_API to3d_status to3d_conv3d_forward(int32_t Z, int32_t Y, int32_t X, int32_t C1, int32_t C2,
+                                         int32_t Cout, const void* in1, const void* in2,
+                                         const void* W, const float* bias, int32_t relu,
+                                         float* out, void* stream);
+/* Backward of the same convolution for upstream gradient gy [v][Cout]
+ * (FP32), masked by act > 0 where act (BF16 [v][Cout], the forward ReLU
+ * output) is not NULL: gw [27][Cout][C1+C2] and gb [Cout] (FP32, added to
+ * what they hold; gb may be NULL) and, if gx is not NULL, gx [v][C1+C2]
+ * (FP32, overwritten).  x1, x2 BF16 forward inputs.  Cout in 16..64 a
+ * multiple of 16, C1 + C2 <= 128.  Enqueued on `stream`. */
+TO3D_API to3d_status to3d_conv3d_backward(int32_t Z, int32_t Y, int32_t X, int32_t C1, int32_t C2,
+                                          int32_t Cout, const void* x1, const void* x2,
+                                          const void* W, const float* gy, const void* act,
+                                          float* gx, float* gw, float* gb, void* stream);
+
 /* ---- many independent problems ------------------------------------------ */
 
 typedef struct to3d_batch to3d_batch;

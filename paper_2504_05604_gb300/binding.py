@@ -86,6 +86,16 @@ _SIGS = {
     "to3d_oc_update": (I32, [VP, VP, VP, VP, DP, DP, C.POINTER(I32), I32]),
     "to3d_sensitivity_noalloc": (I32, [I32, I32, I32, C.c_double, C.c_double, C.c_double,
                                        C.c_double, VP, VP, VP, VP, DP, VP]),
+    "to3d_cnn_init": (I32, [VP, C.c_uint64]),
+    "to3d_cnn_param_count": (I32, [VP, C.POINTER(C.c_int64)]),
+    "to3d_cnn_get_params": (I32, [VP, VP, C.c_int64]),
+    "to3d_cnn_set_params": (I32, [VP, VP, C.c_int64]),
+    "to3d_cnn_apply": (I32, [VP, VP, VP, VP, I32]),
+    "to3d_cnn_train": (I32, [VP, I32, I32, I32, C.c_double, C.c_uint64, I32, DP, DP]),
+    "to3d_cnn_loss_grad": (I32, [VP, VP, VP, VP, I32, VP, C.c_int64, DP]),
+    "to3d_conv3d_forward": (I32, [I32, I32, I32, I32, I32, I32, VP, VP, VP, VP, I32, VP, VP]),
+    "to3d_conv3d_backward": (I32, [I32, I32, I32, I32, I32, I32, VP, VP, VP, VP, VP, VP, VP, VP,
+                                   VP]),
     "to3d_batch_create": (I32, [I32, C.POINTER(Params), C.POINTER(VP), C.POINTER(VP),
                                 C.POINTER(VP), VP, C.POINTER(VP)]),
     "to3d_batch_step": (I32, [VP, C.POINTER(IterInfo)]),
@@ -303,6 +313,99 @@ class Context:
         self._check(self.lib.to3d_oc_update(self.h, ax.ptr, ad.ptr, an.ptr, C.byref(lam),
                                             C.byref(vol), C.byref(nh), dev), "oc_update")
         return xnew, lam.value, vol.value, nh.value
+
+    # ---- learned preconditioner (not in the paper; optional)
+    def cnn_init(self, seed: int = 0):
+        self._check(self.lib.to3d_cnn_init(self.h, seed), "cnn_init")
+
+    def cnn_param_count(self) -> int:
+        n = C.c_int64()
+        self._check(self.lib.to3d_cnn_param_count(self.h, C.byref(n)), "cnn_param_count")
+        return n.value
+
+    def cnn_params(self) -> np.ndarray:
+        p = np.empty(self.cnn_param_count(), np.float32)
+        self._check(self.lib.to3d_cnn_get_params(self.h, p.ctypes.data, p.size), "cnn_params")
+        return p
+
+    def set_cnn_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(self.lib.to3d_cnn_set_params(self.h, p.ctypes.data, p.size), "set_cnn_params")
+
+    def cnn_apply(self, x, r, z=None):
+        z = np.empty(self.ndof) if z is None else z
+        ax, ar, az = _Arg(x, np.float64), _Arg(r, np.float64), _Arg(z, np.float64)
+        dev = _same_kind(ax, ar, az)
+        self._check(self.lib.to3d_cnn_apply(self.h, ax.ptr, ar.ptr, az.ptr, dev), "cnn_apply")
+        return z
+
+    def cnn_loss_grad(self, x, r, e):
+        g = np.empty(self.cnn_param_count(), np.float32)
+        ax, ar, ae = _Arg(x, np.float64), _Arg(r, np.float64), _Arg(e, np.float64)
+        dev = _same_kind(ax, ar, ae)
+        loss = C.c_double()
+        self._check(self.lib.to3d_cnn_loss_grad(self.h, ax.ptr, ar.ptr, ae.ptr, dev,
+                                                g.ctypes.data, g.size, C.byref(loss)),
+                    "cnn_loss_grad")
+        return loss.value, g
+
+    def cnn_train(self, nsnap: int, per_design: int = 8, steps: int = 200, lr: float = 1e-3,
+                  seed: int = 0, source: int = 0):
+        """Take ``nsnap`` residual snapshots (source 0: Jacobi-PCG, 1: flexible
+        CG with the current network) and run ``steps`` Adam steps; returns
+        the mean energy loss of the first and last tenth of the steps."""
+        a, b = C.c_double(), C.c_double()
+        self._check(self.lib.to3d_cnn_train(self.h, nsnap, per_design, steps, lr, seed, source,
+                                            C.byref(a), C.byref(b)), "cnn_train")
+        return a.value, b.value
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return VP(torch.cuda.current_stream().cuda_stream)
+    return VP(stream)
+
+
+def _dev_ptr(t, dtype_name):
+    if t is None:
+        return None
+    if not (_is_torch(t) and t.is_cuda and t.is_contiguous()):
+        raise TypeError("convolution hooks take contiguous CUDA tensors")
+    if str(t.dtype) != "torch." + dtype_name:
+        raise TypeError(f"expected {dtype_name}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def conv3d_forward(in1, W, out, in2=None, bias=None, relu=False, stream=None):
+    """One 3x3x3 convolution (``to3d_conv3d_forward``): channels-last BF16
+    in1 [Z,Y,X,C1] (+ in2 [Z,Y,X,C2]), W BF16 [27,Cout,C1+C2], FP32 bias and
+    out [Z,Y,X,Cout]."""
+    Z, Y, X, C1 = in1.shape
+    C2 = in2.shape[3] if in2 is not None else 0
+    st = load().to3d_conv3d_forward(Z, Y, X, C1, C2, out.shape[3], _dev_ptr(in1, "bfloat16"),
+                                    _dev_ptr(in2, "bfloat16"), _dev_ptr(W, "bfloat16"),
+                                    _dev_ptr(bias, "float32"), int(relu),
+                                    _dev_ptr(out, "float32"), _stream_ptr(stream))
+    if st:
+        raise To3dError(st, "to3d_conv3d_forward")
+    return out
+
+
+def conv3d_backward(x1, W, gy, gw, gb=None, gx=None, x2=None, act=None, stream=None):
+    """Backward of ``conv3d_forward`` (``to3d_conv3d_backward``): gw, gb
+    accumulate, gx is overwritten."""
+    Z, Y, X, C1 = x1.shape
+    C2 = x2.shape[3] if x2 is not None else 0
+    st = load().to3d_conv3d_backward(Z, Y, X, C1, C2, gy.shape[3], _dev_ptr(x1, "bfloat16"),
+                                     _dev_ptr(x2, "bfloat16"), _dev_ptr(W, "bfloat16"),
+                                     _dev_ptr(gy, "float32"), _dev_ptr(act, "bfloat16"),
+                                     _dev_ptr(gx, "float32"), _dev_ptr(gw, "float32"),
+                                     _dev_ptr(gb, "float32"), _stream_ptr(stream))
+    if st:
+        raise To3dError(st, "to3d_conv3d_backward")
+    return gw, gb, gx
+
 
 
 def sensitivity_noalloc(nelx, nely, nelz, x, u, ce, dc, penal=3.0, E0=1.0, Emin=1e-9, nu=0.3,

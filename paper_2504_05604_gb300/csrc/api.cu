@@ -175,6 +175,7 @@ static void free_all(to3d_ctx* c) {
     if (c->dcctl_h) cudaFreeHost(c->dcctl_h);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c->st;
+    destroy_cnn(c);
 }
 
 // Device pointer for an input: the caller's pointer, or a staged copy.
@@ -340,6 +341,7 @@ static to3d_status solve_f64(to3d_ctx* c, const double* f, double fnorm, to3d_so
         if (status != TO3D_OK || relres <= tol || ++restarts > 4 || total >= c->prm.cg_maxit) break;
     }
     if (status == TO3D_OK && relres > tol) status = TO3D_ENOCONV;
+    if (status == TO3D_OK && total > 0) c->pcg_its_est = total;
     if (info) {
         info->iters = total;
         info->outer = restarts + 1;
@@ -441,20 +443,62 @@ static to3d_status solve_dc(to3d_ctx* c, const double* f, double fnorm, to3d_sol
 }
 
 static to3d_status prepare_operator(to3d_ctx* c, const double* x) {
+    c->xop = x;
     launch_simp(c, c->stream, x);
     launch_diag(c, c->stream, c->E);
     LK("simp/diag");
     return TO3D_OK;
 }
 
+namespace to3d {
+to3d_status prepare_op(to3d_ctx* c, const double* x) { return prepare_operator(c, x); }
+
+to3d_status stage_input(to3d_ctx* c, const void* src, size_t bytes, int on_device, size_t slot,
+                        const void** out) {
+    return stage_in(c, src, bytes, on_device, slot, out);
+}
+
+// FP64 Jacobi-PCG from u = 0 for exactly `iters` iterations (rhs f, masked)
+to3d_status run_pcg64_iters(to3d_ctx* c, const double* f, int iters) {
+    launch_fill_zero(c, c->stream, c->u, sizeof(double) * 3 * c->g.nnode);
+    launch_ss_reset(c, c->stream, 0.0, iters);
+    launch_mask_copy(c, c->stream, f, c->r);
+    launch_pcg64_init(c, c->stream);
+    for (int i = 0; i < iters; ++i) launch_pcg64_iter(c, c->stream);
+    return launch_check(c, "pcg64 iterations");
+}
+
+// FP64 Jacobi-PCG of K u = f to relative residual rtol (u starts at 0)
+to3d_status solve64_rtol(to3d_ctx* c, const double* f, double fnorm, double rtol,
+                         to3d_solve_info* info) {
+    const double keep = c->prm.cg_rtol;
+    c->prm.cg_rtol = rtol;
+    launch_fill_zero(c, c->stream, c->u, sizeof(double) * 3 * c->g.nnode);
+    to3d_status st = solve_f64(c, f, fnorm, info);
+    c->prm.cg_rtol = keep;
+    return st;
+}
+
+to3d_status solve_fcg(to3d_ctx* c, const double* f, double fnorm, to3d_solve_info* info);
+}  // namespace to3d
+
 static to3d_status solve_current(to3d_ctx* c, const double* f, double fnorm, to3d_solve_info* info) {
     if (!c->prm.warm_start || !c->have_u)
         launch_fill_zero(c, c->stream, c->u, sizeof(double) * 3 * c->g.nnode);
-    to3d_status st = (c->prm.precision == TO3D_F64) ? solve_f64(c, f, fnorm, info)
-                                                     : solve_dc(c, f, fnorm, info);
+    to3d_status st;
+    if (c->prm.precond == TO3D_CNN_FCG) st = solve_fcg(c, f, fnorm, info);
+    else if (c->prm.precision == TO3D_F64) st = solve_f64(c, f, fnorm, info);
+    else st = solve_dc(c, f, fnorm, info);
     c->have_u = true;
     return st;
 }
+
+namespace to3d {
+// FP64 Jacobi-PCG continuing from the current u (fallback of flexible CG)
+to3d_status solve64_from_u(to3d_ctx* c, const double* f, double fnorm, to3d_solve_info* info) {
+    return solve_f64(c, f, fnorm, info);
+}
+}  // namespace to3d
 
 // ------------------------------------------------------------------ C API
 extern "C" {
@@ -513,7 +557,7 @@ to3d_status to3d_create(const to3d_params* prm, const uint8_t* fixed, const doub
         prm->cg_maxit < 1 || prm->oc_levels < 1 || prm->oc_levels > 5 || prm->precision < 0 ||
         prm->precision > 4 || prm->filter < 0 || prm->filter > 1)
         return TO3D_EINVAL;
-    if (prm->precond != TO3D_JACOBI) return TO3D_EINVAL;
+    if (prm->precond != TO3D_JACOBI && prm->precond != TO3D_CNN_FCG) return TO3D_EINVAL;
 
     to3d_ctx* c = new (std::nothrow) to3d_ctx();
     if (!c) return TO3D_ENOMEM;

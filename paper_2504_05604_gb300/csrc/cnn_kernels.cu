@@ -1,0 +1,345 @@
+// Kernels of the learned preconditioner (see cnn_kernels.cuh).
+#include "cnn_kernels.cuh"
+
+namespace to3d {
+namespace cnn {
+
+// D (16x8, FP32) += A (16x16, BF16, row) * B (16x8, BF16, col)
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// two consecutive channels of one voxel as a packed BF16 pair (0 if v < 0)
+template <bool F32>
+__device__ __forceinline__ uint32_t load_pair(const void* base, long long v, int cs, int c,
+                                              const bf16* mask, int mcs) {
+    if (v < 0) return 0u;
+    uint32_t r;
+    if (F32) {
+        const float2 f = *reinterpret_cast<const float2*>((const float*)base + v * cs + c);
+        r = pack_bf16(f.x, f.y);
+    } else {
+        r = *reinterpret_cast<const uint32_t*>((const bf16*)base + v * cs + c);
+    }
+    if (mask) {
+        const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(mask + v * mcs + c);
+        const uint32_t keep_lo = __bfloat162float(m.x) > 0.f ? 0x0000ffffu : 0u;
+        const uint32_t keep_hi = __bfloat162float(m.y) > 0.f ? 0xffff0000u : 0u;
+        r &= (keep_lo | keep_hi);
+    }
+    return r;
+}
+
+// Implicit-GEMM 3x3x3 convolution: a warp computes 16 voxels x all output
+// channels; K runs over 27 taps x input channels in steps of 16.
+template <bool F32, int NT>
+__global__ void __launch_bounds__(128) k_conv(const ConvArgs a) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+    const long long m0 = (long long)warp * 16;
+    if (m0 >= a.nvox) return;
+    const int Cin = a.C1 + a.C2;
+    long long vrow[2];
+    int cz[2], cy[2], cx[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const long long v = m0 + g + 8 * h;
+        vrow[h] = v < a.nvox ? v : -1;
+        const long long vv = v < a.nvox ? v : 0;
+        cx[h] = (int)(vv % a.X);
+        cy[h] = (int)((vv / a.X) % a.Y);
+        cz[h] = (int)(vv / ((long long)a.X * a.Y));
+    }
+    float acc[NT][4];
+#pragma unroll
+    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+    for (int tap = 0; tap < 27; ++tap) {
+        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        long long nb[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int z = cz[h] + dz, y = cy[h] + dy, x = cx[h] + dx;
+            nb[h] = (vrow[h] >= 0 && z >= 0 && z < a.Z && y >= 0 && y < a.Y && x >= 0 && x < a.X)
+                        ? x + (long long)a.X * (y + (long long)a.Y * z)
+                        : -1;
+        }
+        const bf16* Wt = a.W + (size_t)tap * a.Cout * Cin;
+        for (int k0 = 0; k0 < Cin; k0 += 16) {
+            const bool first = k0 < a.C1;
+            const void* src = first ? a.in1 : a.in2;
+            const int cs = first ? a.C1 : a.C2;
+            const int kk = first ? k0 : k0 - a.C1;
+            const bf16* mk = first ? a.mask1 : nullptr;
+            uint32_t af[4];
+            af[0] = load_pair<F32>(src, nb[0], cs, kk + 2 * q, mk, cs);
+            af[1] = load_pair<F32>(src, nb[1], cs, kk + 2 * q, mk, cs);
+            af[2] = load_pair<F32>(src, nb[0], cs, kk + 2 * q + 8, mk, cs);
+            af[3] = load_pair<F32>(src, nb[1], cs, kk + 2 * q + 8, mk, cs);
+#pragma unroll
+            for (int n = 0; n < NT; ++n) {
+                const bf16* wrow = Wt + (size_t)(n * 8 + g) * Cin + k0 + 2 * q;
+                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wrow);
+                const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wrow + 8);
+                mma16816(acc[n], af, b0, b1);
+            }
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < NT; ++n)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (vrow[h] < 0) continue;
+            const int c = n * 8 + 2 * q;
+            float v0 = acc[n][2 * h], v1 = acc[n][2 * h + 1];
+            if (a.bias) {
+                v0 += a.bias[c];
+                v1 += a.bias[c + 1];
+            }
+            if (a.relu) {
+                v0 = fmaxf(v0, 0.f);
+                v1 = fmaxf(v1, 0.f);
+            }
+            const long long o = vrow[h] * a.out_cstride + a.out_coff + c;
+            if (a.out_b) {
+                *reinterpret_cast<uint32_t*>(a.out_b + o) = pack_bf16(v0, v1);
+            } else if (a.accumulate) {
+                a.out_f[o] += v0;
+                a.out_f[o + 1] += v1;
+            } else {
+                a.out_f[o] = v0;
+                a.out_f[o + 1] = v1;
+            }
+        }
+}
+
+void conv_forward(const ConvArgs& a, bool in_fp32, cudaStream_t s) {
+    const long long warps = (a.nvox + 15) / 16;
+    const unsigned blocks = (unsigned)((warps + 3) / 4);
+    const int nt = a.Cout / 8;
+#define TO3D_CONV(NTV)                                                              \
+    if (nt == NTV) {                                                                \
+        if (in_fp32) k_conv<true, NTV><<<blocks, 128, 0, s>>>(a);                   \
+        else k_conv<false, NTV><<<blocks, 128, 0, s>>>(a);                          \
+        return;                                                                     \
+    }
+    TO3D_CONV(1) TO3D_CONV(2) TO3D_CONV(4) TO3D_CONV(6) TO3D_CONV(8) TO3D_CONV(12) TO3D_CONV(16)
+#undef TO3D_CONV
+}
+
+// Weight (and bias) gradient of a convolution, FP32 on the CUDA cores:
+// gw[tap][co][ci] += sum_v gy[v][co] (mask) x[v + tap][ci].  A block owns a
+// 16 x 16 (co, ci) tile of one tap and a chunk of voxels.
+constexpr int WG_CHUNK = 128;
+constexpr int WG_VOX_PER_BLOCK = 4096;
+
+template <bool XF32>
+__global__ void __launch_bounds__(256) k_wgrad(const WgradArgs a) {
+    __shared__ float sg[WG_CHUNK][17];
+    __shared__ float sx[WG_CHUNK][17];
+    const int tap = blockIdx.y;
+    const int nci = a.Cin / 16;
+    const int co0 = (blockIdx.z / nci) * 16, ci0 = (blockIdx.z % nci) * 16;
+    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const int t = threadIdx.x, tco = t / 16, tci = t % 16;
+    float acc = 0.f, accb = 0.f;
+    const long long vbeg = (long long)blockIdx.x * WG_VOX_PER_BLOCK;
+    const long long vend = min(vbeg + WG_VOX_PER_BLOCK, a.nvox);
+    for (long long v0 = vbeg; v0 < vend; v0 += WG_CHUNK) {
+        for (int i = t; i < WG_CHUNK * 16; i += 256) {
+            const int r = i / 16, c = i % 16;
+            const long long v = v0 + r;
+            float gv = 0.f, xv = 0.f;
+            if (v < vend) {
+                const int co = co0 + c;
+                if (co < a.Cout_fwd) {
+                    gv = a.gy[v * a.gy_cstride + co];
+                    if (a.mask && !(__bfloat162float(a.mask[v * a.gy_cstride + co]) > 0.f)) gv = 0.f;
+                }
+                const int x = (int)(v % a.X), y = (int)((v / a.X) % a.Y), z = (int)(v / ((long long)a.X * a.Y));
+                const int xx = x + dx, yy = y + dy, zz = z + dz;
+                if (xx >= 0 && xx < a.X && yy >= 0 && yy < a.Y && zz >= 0 && zz < a.Z) {
+                    const long long nbv = xx + (long long)a.X * (yy + (long long)a.Y * zz);
+                    const int ci = ci0 + c;
+                    const bool first = ci < a.C1;
+                    const int cs = first ? a.C1 : a.Cin - a.C1;
+                    const int cc = first ? ci : ci - a.C1;
+                    const void* src = first ? a.x1 : a.x2;
+                    xv = XF32 ? ((const float*)src)[nbv * cs + cc]
+                              : __bfloat162float(((const bf16*)src)[nbv * cs + cc]);
+                }
+            }
+            sg[r][c] = gv;
+            sx[r][c] = xv;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int r = 0; r < WG_CHUNK; ++r) {
+            acc = fmaf(sg[r][tco], sx[r][tci], acc);
+            accb += sg[r][tco];
+        }
+        __syncthreads();
+    }
+    const int co = co0 + tco, ci = ci0 + tci;
+    if (co < a.Cout_fwd) {
+        atomicAdd(&a.gw[((size_t)tap * a.Cout_fwd + co) * a.Cin + ci], acc);
+        if (a.gb && tap == 0 && ci0 == 0 && tci == 0) atomicAdd(&a.gb[co], accb);
+    }
+}
+
+void conv_wgrad(const WgradArgs& a, bool x_fp32, cudaStream_t s) {
+    const int ncot = (a.Cout + 15) / 16;
+    dim3 grid((unsigned)((a.nvox + WG_VOX_PER_BLOCK - 1) / WG_VOX_PER_BLOCK), 27,
+              (unsigned)(ncot * (a.Cin / 16)));
+    if (x_fp32) k_wgrad<true><<<grid, 256, 0, s>>>(a);
+    else k_wgrad<false><<<grid, 256, 0, s>>>(a);
+}
+
+// Wt[tap][ci][co] = W[26 - tap][co][ci]: the data gradient is a convolution
+// of the upstream gradient with the flipped, transposed kernel.
+__global__ void k_transpose_flip(const bf16* W, bf16* Wt, int Cout, int Cin) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long n = 27LL * Cout * Cin;
+    if (i >= n) return;
+    const int co = (int)(i % Cout);
+    const int ci = (int)((i / Cout) % Cin);
+    const int tap = (int)(i / ((long long)Cout * Cin));
+    Wt[i] = W[((size_t)(26 - tap) * Cout + co) * Cin + ci];
+}
+
+void transpose_flip(const bf16* W, bf16* Wt, int Cout, int Cin, cudaStream_t s) {
+    const long long n = 27LL * Cout * Cin;
+    k_transpose_flip<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(W, Wt, Cout, Cin);
+}
+
+// ---- 2x2x2 average pooling and nearest x2 upsampling (channels-last)
+__global__ void k_pool2(const bf16* in, bf16* out, int Z, int Y, int X, int C) {
+    const long long n = (long long)(Z / 2) * (Y / 2) * (X / 2) * C;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = (int)(i % C);
+    const long long v = i / C;
+    const int X2 = X / 2, Y2 = Y / 2;
+    const int x = (int)(v % X2), y = (int)((v / X2) % Y2), z = (int)(v / ((long long)X2 * Y2));
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const long long u = (2 * x + (k & 1)) + (long long)X * ((2 * y + ((k >> 1) & 1)) + (long long)Y * (2 * z + (k >> 2)));
+        s += __bfloat162float(in[u * C + c]);
+    }
+    out[i] = __float2bfloat16_rn(0.125f * s);
+}
+
+__global__ void k_pool2_bwd(const float* gout, int gcs, int gco, float* gin, int Z, int Y, int X,
+                            int C, int accumulate) {
+    const long long n = (long long)Z * Y * X * C;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = (int)(i % C);
+    const long long v = i / C;
+    const int x = (int)(v % X), y = (int)((v / X) % Y), z = (int)(v / ((long long)X * Y));
+    const long long p = (x / 2) + (long long)(X / 2) * ((y / 2) + (long long)(Y / 2) * (z / 2));
+    const float g = 0.125f * gout[p * gcs + gco + c];
+    gin[i] = accumulate ? gin[i] + g : g;
+}
+
+__global__ void k_up2(const bf16* in, bf16* out, int Z, int Y, int X, int C) {
+    // in: (Z/2, Y/2, X/2), out: (Z, Y, X)
+    const long long n = (long long)Z * Y * X * C;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = (int)(i % C);
+    const long long v = i / C;
+    const int x = (int)(v % X), y = (int)((v / X) % Y), z = (int)(v / ((long long)X * Y));
+    const long long p = (x / 2) + (long long)(X / 2) * ((y / 2) + (long long)(Y / 2) * (z / 2));
+    out[i] = in[p * C + c];
+}
+
+__global__ void k_up2_bwd(const float* gout, int gcs, int gco, float* gin, int Z, int Y, int X,
+                          int C, int accumulate) {
+    // gout on (Z, Y, X); gin on (Z/2, Y/2, X/2)
+    const int X2 = X / 2, Y2 = Y / 2;
+    const long long n = (long long)(Z / 2) * Y2 * X2 * C;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = (int)(i % C);
+    const long long v = i / C;
+    const int x = (int)(v % X2), y = (int)((v / X2) % Y2), z = (int)(v / ((long long)X2 * Y2));
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const long long u = (2 * x + (k & 1)) + (long long)X * ((2 * y + ((k >> 1) & 1)) + (long long)Y * (2 * z + (k >> 2)));
+        s += gout[u * gcs + gco + c];
+    }
+    gin[i] = accumulate ? gin[i] + s : s;
+}
+
+__global__ void k_add_channels(const float* src, int scs, int sco, float* dst, long long nvox, int C,
+                               int accumulate) {
+    const long long n = nvox * C;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float v = src[(i / C) * scs + sco + (i % C)];
+    dst[i] = accumulate ? dst[i] + v : v;
+}
+
+static unsigned nb(long long n) { return (unsigned)((n + 255) / 256); }
+
+void pool2_forward(const bf16* in, bf16* out, int Z, int Y, int X, int C, cudaStream_t s) {
+    k_pool2<<<nb((long long)(Z / 2) * (Y / 2) * (X / 2) * C), 256, 0, s>>>(in, out, Z, Y, X, C);
+}
+void pool2_backward(const float* gout, int gcs, int gco, float* gin, int Z, int Y, int X, int C,
+                    int accumulate, cudaStream_t s) {
+    k_pool2_bwd<<<nb((long long)Z * Y * X * C), 256, 0, s>>>(gout, gcs, gco, gin, Z, Y, X, C, accumulate);
+}
+void up2_forward(const bf16* in, bf16* out, int Z, int Y, int X, int C, cudaStream_t s) {
+    k_up2<<<nb((long long)Z * Y * X * C), 256, 0, s>>>(in, out, Z, Y, X, C);
+}
+void up2_backward(const float* gout, int gcs, int gco, float* gin, int Z, int Y, int X, int C,
+                  int accumulate, cudaStream_t s) {
+    k_up2_bwd<<<nb((long long)(Z / 2) * (Y / 2) * (X / 2) * C), 256, 0, s>>>(gout, gcs, gco, gin, Z, Y, X, C, accumulate);
+}
+void add_channels(const float* src, int scs, int sco, float* dst, long long nvox, int C,
+                  int accumulate, cudaStream_t s) {
+    k_add_channels<<<nb(nvox * C), 256, 0, s>>>(src, scs, sco, dst, nvox, C, accumulate);
+}
+
+// ---- Adam on a flat FP32 parameter vector
+__global__ void k_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1,
+                       float b2, float eps, float c1, float c2) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+void adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
+          float eps, int t, cudaStream_t s) {
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    k_adam<<<nb(n), 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+}
+
+__global__ void k_to_bf16(const float* src, bf16* dst, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+void to_bf16(const float* src, bf16* dst, long long n, cudaStream_t s) {
+    k_to_bf16<<<nb(n), 256, 0, s>>>(src, dst, n);
+}
+
+}  // namespace cnn
+}  // namespace to3d

@@ -85,6 +85,8 @@ struct to3d_ctx {
     int iter = 0;
     bool trace = false;
     bool have_u = false;
+    int pcg_its_est = 0;           // iterations of the last FP64 Jacobi-PCG solve (0: none yet)
+    const double* xop = nullptr;   // densities the operator was last prepared for (device)
     bool have_dinv = false;
 
     to3d::KE64 ke;                        // unit-modulus element stiffness
@@ -149,6 +151,7 @@ struct to3d_ctx {
     cudaStream_t cap_stream2 = nullptr, cap_stream3 = nullptr;   // nested loop-body captures
     void* dcctl = nullptr;                // device control block of the graph's solver
     void* dcctl_h = nullptr;              // pinned copy of it
+    void* cnn = nullptr;                  // learned preconditioner (network, workspaces)
 };
 
 // ---------------------------------------------------------------- launchers
@@ -200,6 +203,15 @@ void launch_sensitivity_raw(const KE64& ke, const Grid& g, cudaStream_t s, const
                             const double* u, double penal, double E0, double Emin, double* ce,
                             double* dc, const Reducer& red, double* comp_out);
 bool unit_ke(double nu, KE64* out);
+// solver helpers shared with the learned-preconditioner code
+to3d_status prepare_op(to3d_ctx* c, const double* x);
+to3d_status stage_input(to3d_ctx* c, const void* src, size_t bytes, int on_device, size_t slot,
+                        const void** out);
+to3d_status run_pcg64_iters(to3d_ctx* c, const double* f, int iters);
+to3d_status solve64_rtol(to3d_ctx* c, const double* f, double fnorm, double rtol,
+                         to3d_solve_info* info);
+to3d_status solve64_from_u(to3d_ctx* c, const double* f, double fnorm, to3d_solve_info* info);
+void destroy_cnn(to3d_ctx* c);
 constexpr int kElementThreads = 256;   // threads per block of the element kernels
 void launch_filter(to3d_ctx* c, cudaStream_t s, int mode, const double* a, const double* b,
                    double* out);
