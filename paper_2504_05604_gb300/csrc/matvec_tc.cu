@@ -172,8 +172,8 @@ struct TcSmemWs {
     static constexpr int STAGES = 0;
     static constexpr int A = STAGES + NS * TC_STAGE_BYTES;
     static constexpr int B = A + 2 * NSL * TC_A_BYTES;
-    static constexpr int Z = B + NMMA * 64;                       // [4 warps][16][6] floats
-    static constexpr int BAR = Z + 4 * 16 * 6 * 4;
+    static constexpr int Z = B + NMMA * 64;                       // [2][4 warps][16][6] floats
+    static constexpr int BAR = Z + 2 * 4 * 16 * 6 * 4;
     static constexpr int NBAR = 3 * NS + 8;
     static constexpr int TADDR = BAR + 8 * NBAR;
     static constexpr int USED = TADDR + 16;
@@ -222,14 +222,14 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
     if (tid == 0) {
         for (int i = 0; i < NS; ++i) {
             tc::mbar_init(&full[i], 1);
-            tc::mbar_init(&empty[i], 2);
+            tc::mbar_init(&empty[i], 8);      // one arrival per builder and epilogue warp
             tc::mbar_init(&conv[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
-            tc::mbar_init(&afull[i], 1);
+            tc::mbar_init(&afull[i], 4);      // one arrival per builder warp
             tc::mbar_init(&aempty[i], 1);
             tc::mbar_init(&dfull[i], 1);
-            tc::mbar_init(&dempty[i], 1);
+            tc::mbar_init(&dempty[i], 4);     // one arrival per epilogue warp
         }
         s_fail = 0;
         tc::fence_mbar_init();
@@ -326,7 +326,15 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
         // ------------------------------------------------ builders
         const int ei = tid % TC_EX, ej = tid / TC_EX;
         uint32_t G = 0, H = 0;
-        auto convert = [&](uint32_t Gm, int m, int i0, int j0, int k0, int nown, int xo) -> bool {
+        // Each thread converts the float4 chunks idx = tid and tid + 128 of
+        // a stage (3 components x 9 rows x 5 chunks).  A chunk of an owned
+        // node row that holds at least one owned node is stored whole to
+        // p_new: it is 16-byte aligned in global memory (the box starts on a
+        // multiple of 4 nodes), and its other nodes are halo or pad nodes
+        // whose values the owning tile computes bit for bit the same.
+        constexpr int Q = TC_PLANE / 4;
+        long long goff[2];
+        auto convert = [&](uint32_t Gm, int m, int k0, int nown) -> bool {
             const int s = Gm % NS;
             if (!wait(&full[s], (Gm / NS) & 1u)) return false;
             if (FUSED) {
@@ -335,29 +343,21 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
                 const float4* R = (const float4*)(st + TC_STAGE_R);
                 const float4* D = (const float4*)(st + TC_STAGE_D);
                 const bool owned_layer = m >= 1 && m <= nown;
-                const long long zoff = (long long)a.px * ((long long)g.ny * (k0 - 1 + m));
-                constexpr int Q = TC_PLANE / 4;
-                for (int idx = tid; idx < 3 * Q; idx += 128) {
-                    const int c = idx / Q, rem = idx - c * Q;
-                    const float4 d4 = D[rem], r4 = R[idx], p4 = P[idx];
-                    float4 v;
-                    v.x = fmaf(zcoef * d4.x, r4.x, beta * p4.x);
-                    v.y = fmaf(zcoef * d4.y, r4.y, beta * p4.y);
-                    v.z = fmaf(zcoef * d4.z, r4.z, beta * p4.z);
-                    v.w = fmaf(zcoef * d4.w, r4.w, beta * p4.w);
-                    P[idx] = v;
-                    const int yy = rem / (TC_BOXX / 4), x0 = 4 * (rem - yy * (TC_BOXX / 4));
-                    if (owned_layer && yy >= 1 && yy <= TC_BY) {
-                        const int gj = j0 - 1 + yy;
-                        if (gj < g.ny) {
-                            float* dst = a.p_new + c * a.vol + zoff + (long long)a.px * gj;
-                            const float vv[4] = {v.x, v.y, v.z, v.w};
+                const long long zoff = a.plane * (long long)(k0 - 1 + m);
 #pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                const int li = x0 + u - xo, gi = i0 - 1 + li;
-                                if (li >= 1 && li <= TC_BX && gi < g.nx) dst[gi] = vv[u];
-                            }
-                        }
+                for (int k = 0; k < 2; ++k) {
+                    const int idx = tid + 128 * k;
+                    if (idx < 3 * Q) {
+                        const int c = idx / Q, rem = idx - c * Q;
+                        const float4 d4 = D[rem], r4 = R[idx], p4 = P[idx];
+                        float4 v;
+                        v.x = fmaf(zcoef * d4.x, r4.x, beta * p4.x);
+                        v.y = fmaf(zcoef * d4.y, r4.y, beta * p4.y);
+                        v.z = fmaf(zcoef * d4.z, r4.z, beta * p4.z);
+                        v.w = fmaf(zcoef * d4.w, r4.w, beta * p4.w);
+                        P[idx] = v;
+                        if (owned_layer && goff[k] >= 0)
+                            *reinterpret_cast<float4*>(a.p_new + goff[k] + zoff) = v;
                     }
                 }
             }
@@ -369,7 +369,24 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
             const int xs = ((i0 - 1) >= 0) ? ((i0 - 1) & ~3) : -4;
             const int xo = (i0 - 1) - xs;
             const uint32_t Gb = G;
-            bool ok = convert(Gb, 0, i0, j0, k0, nown, xo) && convert(Gb + 1, 1, i0, j0, k0, nown, xo);
+            if (FUSED) {
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    goff[k] = -1;
+                    const int idx = tid + 128 * k;
+                    if (idx < 3 * Q) {
+                        const int c = idx / Q, rem = idx - c * Q;
+                        const int yy = rem / (TC_BOXX / 4), x0 = 4 * (rem - yy * (TC_BOXX / 4));
+                        const int gj = j0 - 1 + yy, gx = xs + x0;
+                        // local node index li = x0 + u - xo; owned: 1 <= li <= 15, gi < nx
+                        const int lo_li = max(x0 - xo, 1), hi_li = min(x0 + 3 - xo, TC_BX);
+                        const bool any_owned = lo_li <= hi_li && i0 - 1 + lo_li < g.nx;
+                        if (yy >= 1 && yy <= TC_BY && gj < g.ny && gx >= 0 && gx < a.px && any_owned)
+                            goff[k] = c * a.vol + (long long)a.px * gj + gx;
+                    }
+                }
+            }
+            bool ok = convert(Gb, 0, k0, nown) && convert(Gb + 1, 1, k0, nown);
             named_bar(1, 128);
             if (!ok || *vfail) break;
             if (tid == 0) {
@@ -378,7 +395,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
             }
             for (int l = 0; l <= nown; ++l, ++H) {
                 if (l >= 1) {
-                    ok = convert(Gb + l + 1, l + 1, i0, j0, k0, nown, xo);
+                    ok = convert(Gb + l + 1, l + 1, k0, nown);
                     named_bar(1, 128);
                     if (!ok || *vfail) break;
                     if (tid == 0) mbar_arrive(&conv[(Gb + l + 1) % NS]);
@@ -428,8 +445,8 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
                     store_row<BF>(At + TC_A_BYTES, tid, r2);
                 }
                 tc::fence_proxy_async_smem();
-                named_bar(1, 128);
-                if (tid == 0) {
+                __syncwarp();
+                if (lane == 0) {
                     mbar_arrive(&afull[b]);
                     mbar_arrive(&empty[(Gb + l) % NS]);
                     if (l == nown) mbar_arrive(&empty[(Gb + l + 1) % NS]);
@@ -452,6 +469,12 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
             const int xo = (i0 - 1) - xs;
             const uint32_t Gb = G;
             float carry0 = 0.f, carry1 = 0.f, carry2 = 0.f, tdot = 0.f;
+            // this thread's node: row nrow_t of the tile, global (gi, gj); q
+            // index of node layer 0 of the tile (one plane per layer above)
+            const int nrow_t = 2 * ew + 1 + (lane >= 16 ? 1 : 0);
+            const int gi_t = i0 + ei - 1, gj_t = j0 + nrow_t - 1;
+            const bool store_node = node_thread && gi_t < g.nx && gj_t < g.ny;
+            const long long qoff = gi_t + (long long)a.px * (gj_t + (long long)g.ny * (k0 - 1));
             bool ok = true;
             for (int l = 0; l <= nown; ++l, ++H) {
                 const int b = H & 1;
@@ -479,8 +502,8 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
                     }
                 }
                 tc::tc_fence_before();
-                named_bar(2, 128);
-                if (et == 0) mbar_arrive(&dempty[b]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&dempty[b]);
                 const uint32_t Gl = Gb + l;
                 if (!wait(&full[Gl % NS], (Gl / NS) & 1u)) { ok = false; break; }
                 float Ecur = reinterpret_cast<const float*>(stages + (Gl % NS) * TC_STAGE_BYTES +
@@ -513,6 +536,10 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
                 // the upper half's b = 0 parts; the upper half (row 2w+1)
                 // finishes node row 2w+2 with the next warp's lower b = 0 parts
                 const bool upper = lane >= 16;
+                // double-buffered by layer parity: one barrier per layer
+                // orders the writes before the reads, and a warp can only
+                // rewrite a buffer after every warp passed the next barrier
+                float* sZb = sZ + (H & 1) * (4 * 16 * 6);
                 float N[2][3];
 #pragma unroll
                 for (int cc = 0; cc < 2; ++cc)
@@ -525,25 +552,23 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
 #pragma unroll
                     for (int cc = 0; cc < 2; ++cc)
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) sZ[(ew * 16 + ei) * 6 + 3 * cc + k] = X[0][cc][k];
+                        for (int k = 0; k < 3; ++k) sZb[(ew * 16 + ei) * 6 + 3 * cc + k] = X[0][cc][k];
                 }
                 named_bar(2, 128);
                 if (upper && ew < 3) {
 #pragma unroll
                     for (int cc = 0; cc < 2; ++cc)
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) N[cc][k] += sZ[((ew + 1) * 16 + ei) * 6 + 3 * cc + k];
+                        for (int k = 0; k < 3; ++k) N[cc][k] += sZb[((ew + 1) * 16 + ei) * 6 + 3 * cc + k];
                 }
                 // z: node layer l = carry (c = 1 halves of layer l-1) + c = 0 halves
                 const float s0 = carry0 + N[0][0], s1 = carry1 + N[0][1], s2 = carry2 + N[0][2];
                 carry0 = N[1][0];
                 carry1 = N[1][1];
                 carry2 = N[1][2];
-                const int nrow = 2 * ew + 1 + (upper ? 1 : 0);            // node row in the tile
-                if (node_thread) {
-                    const int gi = i0 + ei - 1, gj = j0 + nrow - 1, gk = k0 - 1 + l;
-                    if (l >= 1 && gi < g.nx && gj < g.ny) {
-                        const long long pidx = gi + (long long)a.px * (gj + (long long)g.ny * gk);
+                if (store_node && l >= 1) {
+                    {
+                        const long long pidx = qoff + a.plane * (long long)l;
                         a.q[pidx] = s0;
                         a.q[pidx + a.vol] = s1;
                         a.q[pidx + 2 * a.vol] = s2;
@@ -551,17 +576,17 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
                             const uint32_t Gm = Gb + l;
                             if (!wait(&conv[Gm % NS], (Gm / NS) & 1u)) ok = false;
                             const float* pn = (const float*)(stages + (Gm % NS) * TC_STAGE_BYTES + TC_STAGE_P) +
-                                              (xo + ei) + TC_BOXX * nrow;
+                                              (xo + ei) + TC_BOXX * nrow_t;
                             tdot = fmaf(pn[0], s0, fmaf(pn[TC_PLANE], s1, fmaf(pn[2 * TC_PLANE], s2, tdot)));
                         }
                     }
                 }
-                named_bar(2, 128);
-                if (et == 0) mbar_arrive(&empty[(Gb + l) % NS]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[(Gb + l) % NS]);
                 if (!ok) break;
             }
             if (!ok) break;
-            if (et == 0) mbar_arrive(&empty[(Gb + nown + 1) % NS]);
+            if (lane == 0) mbar_arrive(&empty[(Gb + nown + 1) % NS]);
             dot += (double)tdot;
             G = Gb + nown + 2;
         }
