@@ -174,7 +174,7 @@ struct TcSmemWs {
     static constexpr int B = A + 2 * NSL * TC_A_BYTES;
     static constexpr int Z = B + NMMA * 64;                       // [2][4 warps][16][6] floats
     static constexpr int BAR = Z + 2 * 4 * 16 * 6 * 4;
-    static constexpr int NBAR = 3 * NS + 8;
+    static constexpr int NBAR = 3 * NS + 4 + 2 * 4;
     static constexpr int TADDR = BAR + 8 * NBAR;
     static constexpr int USED = TADDR + 16;
     static constexpr int BYTES = 1024 + USED;
@@ -190,6 +190,9 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
     constexpr bool SCALED = (PREC == 3 || PREC == 4);
     constexpr int NMMA = SPLIT ? 64 : 32;            // split: A_lam rows, A_mu rows, 16 spare
     constexpr int TCOLS = SPLIT ? 64 : 32;           // TMEM columns per accumulator
+    // accumulators in flight: 4 x 32 columns (3 CTAs per SM use 384 of the
+    // 512 TMEM columns); the split form's 64-column ones allow 2
+    constexpr int ND = SPLIT ? 2 : 4;
     using L = TcSmemWs<NSL, NMMA>;
     constexpr int NS = L::NS;
     if (FUSED && a.ss->done) return;
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
     uint64_t* afull = conv + NS;
     uint64_t* aempty = afull + 2;
     uint64_t* dfull = aempty + 2;
-    uint64_t* dempty = dfull + 2;
+    uint64_t* dempty = dfull + ND;
     uint32_t* s_taddr = (uint32_t*)(sm + L::TADDR);
     __shared__ double sh[32];
     __shared__ double dout[1];
@@ -216,7 +219,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
     const Grid& g = a.g;
 
     if (warp == 0) {
-        tc::tmem_alloc(s_taddr, 2 * TCOLS);
+        tc::tmem_alloc(s_taddr, ND * TCOLS);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
@@ -228,6 +231,8 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
         for (int i = 0; i < 2; ++i) {
             tc::mbar_init(&afull[i], 4);      // one arrival per builder warp
             tc::mbar_init(&aempty[i], 1);
+        }
+        for (int i = 0; i < ND; ++i) {
             tc::mbar_init(&dfull[i], 1);
             tc::mbar_init(&dempty[i], 4);     // one arrival per epilogue warp
         }
@@ -303,11 +308,11 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
                 int i0, j0, k0, nown;
                 tile_geom(tile, i0, j0, k0, nown);
                 for (int l = 0; l <= nown; ++l, ++H) {
-                    const int b = H & 1;
+                    const int b = H & 1, db = H % ND;
                     if (!wait(&afull[b], (H >> 1) & 1u)) break;
-                    if (!wait(&dempty[b], ((H >> 1) & 1u) ^ 1u)) break;
+                    if (!wait(&dempty[db], ((H / ND) & 1u) ^ 1u)) break;
                     tc::tc_fence_after();
-                    const uint32_t d_tmem = tmem + (uint32_t)(b * TCOLS);
+                    const uint32_t d_tmem = tmem + (uint32_t)(db * TCOLS);
 #pragma unroll
                     for (int s = 0; s < NSL; ++s)
 #pragma unroll
@@ -317,7 +322,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
                                            tc::make_desc_kmajor(b_addr + kk * 256, 128, 512), idesc,
                                            (s | kk) ? 1u : 0u);
                         }
-                    tc::mma_commit(&dfull[b]);
+                    tc::mma_commit(&dfull[db]);
                     tc::mma_commit(&aempty[b]);
                 }
             }
@@ -477,10 +482,10 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
             const long long qoff = gi_t + (long long)a.px * (gj_t + (long long)g.ny * (k0 - 1));
             bool ok = true;
             for (int l = 0; l <= nown; ++l, ++H) {
-                const int b = H & 1;
-                if (!wait(&dfull[b], (H >> 1) & 1u)) { ok = false; break; }
+                const int db = H % ND;
+                if (!wait(&dfull[db], (H / ND) & 1u)) { ok = false; break; }
                 tc::tc_fence_after();
-                const uint32_t trow = tmem + (uint32_t)(b * TCOLS) + ((uint32_t)(ew * 32) << 16);
+                const uint32_t trow = tmem + (uint32_t)(db * TCOLS) + ((uint32_t)(ew * 32) << 16);
                 float dcol[SPLIT ? 64 : 32];
                 if (SPLIT) {
                     float d0[32], d1[32];
@@ -503,7 +508,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
                 }
                 tc::tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&dempty[b]);
+                if (lane == 0) mbar_arrive(&dempty[db]);
                 const uint32_t Gl = Gb + l;
                 if (!wait(&full[Gl % NS], (Gl / NS) & 1u)) { ok = false; break; }
                 float Ecur = reinterpret_cast<const float*>(stages + (Gl % NS) * TC_STAGE_BYTES +
@@ -596,7 +601,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-    if (warp == 0) tc::tmem_dealloc(tmem, 2 * TCOLS);
+    if (warp == 0) tc::tmem_dealloc(tmem, ND * TCOLS);
 
     if (FUSED) {
         double vv[1] = {dot};
