@@ -90,7 +90,11 @@ typedef struct {
     int32_t precond;     /* to3d_precond                                      */
     int32_t oc_levels;   /* bisection levels resolved per reduction pass, 1-6 */
     int32_t warm_start;  /* 1: start each solve from the previous u           */
-    int32_t reserved[6];
+    int32_t fcg_ref_iters; /* TO3D_CNN_FCG: Jacobi-PCG iterations at cg_rtol
+                            * that flexible CG must keep pace with before the
+                            * context has timed a plain solve of its own (0:
+                            * no such bound until then)                       */
+    int32_t reserved[5];
 } to3d_params;
 
 typedef struct {
@@ -222,8 +226,8 @@ TO3D_API to3d_status to3d_oc_update(to3d_ctx* ctx, const double* x, const double
  * when a curvature p^T K p is non-positive, when the smallest residual seen
  * drops by less than 10 % over 200 iterations, or when, past 50
  * iterations, it is 10x above where the context's last plain Jacobi-PCG
- * solve (its iteration count at the same tolerance) would have been at its
- * average rate; to3d_solve_info.outer is then 2 (the fallback starts from
+ * solve (its iteration count at the same tolerance; before there is one,
+ * params.fcg_ref_iters) would have been at its average rate; to3d_solve_info.outer is then 2 (the fallback starts from
  * zero unless the true residual is already below 1e-2 |f|).  The true FP64
  * residual decides convergence. */
 

@@ -35,7 +35,7 @@ class Params(C.Structure):
                 ("inner_rtol", C.c_double),
                 ("cg_maxit", C.c_int32), ("filter", C.c_int32), ("precision", C.c_int32),
                 ("precond", C.c_int32), ("oc_levels", C.c_int32), ("warm_start", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("fcg_ref_iters", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class IterInfo(C.Structure):

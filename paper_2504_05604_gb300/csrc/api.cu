@@ -555,7 +555,7 @@ to3d_status to3d_create(const to3d_params* prm, const uint8_t* fixed, const doub
         !(prm->E0 > 0) || !(prm->Emin > 0) || !(prm->Emin < prm->E0) || !(prm->nu > -1) ||
         !(prm->nu < 0.5) || !(prm->move > 0) || !(prm->bisect_tol > 0) || !(prm->cg_rtol > 0) ||
         prm->cg_maxit < 1 || prm->oc_levels < 1 || prm->oc_levels > 5 || prm->precision < 0 ||
-        prm->precision > 4 || prm->filter < 0 || prm->filter > 1)
+        prm->precision > 4 || prm->filter < 0 || prm->filter > 1 || prm->fcg_ref_iters < 0)
         return TO3D_EINVAL;
     if (prm->precond != TO3D_JACOBI && prm->precond != TO3D_CNN_FCG) return TO3D_EINVAL;
 

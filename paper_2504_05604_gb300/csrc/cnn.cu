@@ -625,7 +625,8 @@ struct FcgRun {
 // iterations (|r| of CG-type methods is not monotone, and plain Jacobi-PCG
 // on SIMP designs can plateau for some 50 iterations), or when it loses to
 // Jacobi-PCG: past 50 iterations, the smallest |r| is 10x above what the
-// context's last plain solve would have reached at its average rate.
+// context's last plain solve (else params.fcg_ref_iters) would have reached
+// at its average rate.
 static to3d_status fcg_run(to3d_ctx* c, const double* f, int max_its, double rr_stop,
                            bool stall_check, double rtol, FcgRun* out) {
     Net* n = net_of(c);
@@ -659,6 +660,7 @@ static to3d_status fcg_run(to3d_ctx* c, const double* f, int max_its, double rr_
     CK_RET(cudaMemcpyAsync(c->p, n->z, sizeof(double) * ndof, cudaMemcpyDeviceToDevice, s));
     double best = rr;
     std::vector<double> marks(1, rr);     // smallest |r|^2 seen, every 50 iterations
+    const int ref_its = c->pcg_its_est > 0 ? c->pcg_its_est : c->prm.fcg_ref_iters;
     if (c->trace) std::fprintf(stderr, "to3d: fcg start |r|^2 %.3e\n", rr);
     while (rr > rr_stop && R.its < max_its) {
         if (!(rz > 0.0)) {
@@ -699,8 +701,8 @@ static to3d_status fcg_run(to3d_ctx* c, const double* f, int max_its, double rr_
         best = std::fmin(best, rr);
         // losing to Jacobi-PCG: after 50 iterations, |r| is 10x above where
         // the last plain solve's average rate would have brought it
-        if (stall_check && c->pcg_its_est > 0 && R.its >= 50 && R.its % 10 == 0 &&
-            best > 100.0 * marks[0] * std::pow(rtol * rtol, (double)R.its / c->pcg_its_est)) {
+        if (stall_check && ref_its > 0 && R.its >= 50 && R.its % 10 == 0 &&
+            best > 100.0 * marks[0] * std::pow(rtol * rtol, (double)R.its / ref_its)) {
             R.broke = true;
             R.why = "slower than Jacobi-PCG";
             break;
