@@ -150,7 +150,7 @@ __device__ __forceinline__ void named_bar(int id, int n) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(bar)) : "memory");
 }
-constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
+constexpr uint32_t TC_WAIT_POLLS = 1u << 20;
 
 // Warp roles: warps 0-3 build (direction update + A rows), warps 4-7 run the
 // epilogue (TMEM -> scaled rows -> node assembly), warp 8 lane 0 issues TMA,
@@ -256,9 +256,13 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
     volatile int* vfail = &s_fail;
     double dot = 0.0;
 
+    // Waits suspend the warp (up to 1 us per poll) rather than spin, so
+    // waiting roles leave the issue slots to the working ones; 2^20 polls
+    // bound a wait to about a second even if suspension were not honoured
+    // for the full hint.
     auto wait = [&](uint64_t* bar, uint32_t par) -> bool {
         if (*vfail) return false;
-        if (tc::mbar_wait_bounded(bar, par, TC_WAIT_LIMIT)) return true;
+        if (tc::mbar_wait_sleep_bounded(bar, par, TC_WAIT_POLLS, 1000u)) return true;
         *vfail = 1;
         return false;
     };
