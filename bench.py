@@ -206,6 +206,13 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+# DRAM bytes (read + write) of one launch of the fused BF16 hi+lo tensor-core
+# kernel at 480x160x80 from one ncu capture of the current kernel
+# (profiles/k_matvec_tc_bf16x2_480x160x80.md); reported only for that form
+# and size.
+TC_TRAFFIC_BYTES = {(2, 480, 160, 80): 232_763_904 + 130_060_032}
+
+
 def algorithmic_bytes_tc(nelx, nely, nelz):
     """Per launch of the fused tensor-core matvec + direction kernel:
     read r, p_old (4 B/dof each), M^-1 (4 B/node), E (4 B/element); write
@@ -375,7 +382,7 @@ def ours(args):
         b = algorithmic_bytes_tc(nelx, nely, nelz)
         ach = b / (tc_avg_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "kernel": "k_matvec_tc (fused direction + tensor-core K p)",
+                "traffic": TC_TRAFFIC_BYTES.get((args.precision, nelx, nely, nelz)), "kernel": "k_matvec_tc (fused direction + tensor-core K p)",
                 "launch_ms": tc_avg_ms, "algorithmic_bytes": b, "samples": tc_n,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
     cpu = None
