@@ -213,6 +213,22 @@ def reference_arm(args):
 TC_TRAFFIC_BYTES = {(2, 480, 160, 80): 232_763_904 + 130_060_032}
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest value of x over all ranks (x itself on one process): the
+    job's time is its slowest replica's."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, steps: int, ms: float) -> float:
+    """Whole-job OC iterations per second: every replica runs `steps`."""
+    return world * steps / (ms / 1000.0)
+
+
 def algorithmic_bytes_tc(nelx, nely, nelz):
     """Per launch of the fused tensor-core matvec + direction kernel:
     read r, p_old (4 B/dof each), M^-1 (4 B/node), E (4 B/element); write
@@ -305,11 +321,8 @@ def ours(args):
         ms = ev0.elapsed_time(ev1)
         launches = ctx.launches - l0
         tc_ms, tc_n = ctx.kernel_stats(0)
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
-    value = world * args.steps / (ms / 1000.0)
+    ms = max_over_ranks(ms, dev)
+    value = job_value(world, args.steps, ms)
     status = max(r["status"] for r in recs)
     its = [r["cg_iters"] + r["outer_iters"] for r in recs]
 
@@ -334,10 +347,8 @@ def ours(args):
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         ctx_e.close()
-        t = torch.tensor([te], device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * args.steps / float(t.item()), "unit": UNIT,
+        te = max_over_ranks(te, dev)
+        e2e = {"value": job_value(world, args.steps, 1000.0 * te), "unit": UNIT,
                "h2d_bytes_per_step": 8 * prob.nel,
                "d2h_bytes_per_step": 8 * prob.nel + 112}
 
