@@ -239,6 +239,26 @@ def algorithmic_bytes_tc(nelx, nely, nelz):
     return 4 * n * 4 + 4 * N + 4 * nel
 
 
+def cnn_flops(nelx, nely, nelz):
+    """Algorithmic FLOPs of one U-Net application on the node grid padded to
+    multiples of 8: 2 * 27 * C_in * C_out per voxel and layer, with the real
+    4 input and 3 output channels (the kernels pad them to 16)."""
+    pad = lambda n: (n + 1 + 7) // 8 * 8
+    v0 = pad(nelx) * pad(nely) * pad(nelz)
+    layers = [(4, 16, 0), (16, 16, 0), (16, 32, 1), (32, 32, 1), (32, 64, 2), (64, 64, 2),
+              (64, 64, 3), (64, 64, 3), (128, 64, 2), (64, 64, 2), (96, 32, 1), (32, 32, 1),
+              (48, 16, 0), (16, 16, 0), (16, 3, 0)]
+    return sum(2 * 27 * ci * co * v0 / 8 ** lev for ci, co, lev in layers)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
 def learned_leg(args, prob, stream, x_start, fp64_iters):
     """One OC iteration of the learned-FCG form from the design the main run
     reached: the U-Net preconditioner (trained first, on the GPU, on residual
@@ -260,6 +280,27 @@ def learned_leg(args, prob, stream, x_start, fp64_iters):
                                 fcg_ref_iters=int(fp64_iters))
     lctx.set_cnn_params(flat)
     lctx.set_density(x_start)
+    # one network application at full size (device buffers), CUDA events
+    xd = torch.as_tensor(x_start, device="cuda")
+    rd = torch.randn(prob.ndof, dtype=torch.float64, device="cuda")
+    zd = torch.empty_like(rd)
+    with torch.cuda.stream(stream):
+        lctx.cnn_apply(xd, rd, zd)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(3):
+            lctx.cnn_apply(xd, rd, zd)
+        a1.record(stream)
+    torch.cuda.synchronize()
+    apply_ms = a0.elapsed_time(a1) / 3
+    flops = cnn_flops(prob.nelx, prob.nely, prob.nelz)
+    peaks = _peaks()
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    cnn_apply = {"ms": apply_ms, "algorithmic_tflop": flops / 1e12,
+                 "achieved_tflops": flops / (apply_ms * 1e-3) / 1e12, "peak_tflops": bf16,
+                 "frac": flops / (apply_ms * 1e-3) / 1e12 / bf16, "bound": "tensor",
+                 "note": "whole U-Net incl. input/output and pooling kernels; convolutions on "
+                         "mma.sync BF16 tiles"}
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -271,7 +312,8 @@ def learned_leg(args, prob, stream, x_start, fp64_iters):
     return {"value": 1000.0 / ms, "unit": UNIT, "cg_iters": r["cg_iters"],
             "fell_back_to_jacobi_pcg": r["outer_iters"] == 2, "relres": r["relres"],
             "status": r["status"], "train_s": train_s, "train_loss_first": first,
-            "train_loss_last": last, "trained_on": "cantilever 96x32x16, 24 snapshots, 1500 Adam steps"}
+            "train_loss_last": last, "trained_on": "cantilever 96x32x16, 24 snapshots, 1500 Adam steps",
+            "cnn_apply": cnn_apply}
 
 
 def ours(args):
