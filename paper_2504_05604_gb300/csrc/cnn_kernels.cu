@@ -19,86 +19,104 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// two consecutive channels of one voxel as a packed BF16 pair (0 if v < 0)
-template <bool F32>
-__device__ __forceinline__ uint32_t load_pair(const void* base, long long v, int cs, int c,
-                                              const bf16* mask, int mcs) {
-    if (v < 0) return 0u;
-    uint32_t r;
-    if (F32) {
-        const float2 f = *reinterpret_cast<const float2*>((const float*)base + v * cs + c);
-        r = pack_bf16(f.x, f.y);
-    } else {
-        r = *reinterpret_cast<const uint32_t*>((const bf16*)base + v * cs + c);
-    }
-    if (mask) {
-        const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(mask + v * mcs + c);
-        const uint32_t keep_lo = __bfloat162float(m.x) > 0.f ? 0x0000ffffu : 0u;
-        const uint32_t keep_hi = __bfloat162float(m.y) > 0.f ? 0xffff0000u : 0u;
-        r &= (keep_lo | keep_hi);
-    }
-    return r;
+// keep the BF16 halves of v whose mask halves are > 0
+__device__ __forceinline__ uint32_t mask_pair(uint32_t v, uint32_t m) {
+    const __nv_bfloat162 mm = *reinterpret_cast<const __nv_bfloat162*>(&m);
+    const uint32_t keep_lo = __bfloat162float(mm.x) > 0.f ? 0x0000ffffu : 0u;
+    const uint32_t keep_hi = __bfloat162float(mm.y) > 0.f ? 0xffff0000u : 0u;
+    return v & (keep_lo | keep_hi);
 }
 
-// Implicit-GEMM 3x3x3 convolution: a warp computes 16 voxels x all output
-// channels; K runs over 27 taps x input channels in steps of 16.
+// Implicit-GEMM 3x3x3 convolution.  A block computes a 16 x 4 x 2 tile of
+// output voxels (8 warps, one 16-voxel x-row each: the M = 16 rows of the
+// MMA) for all output channels.  The input tile with its one-voxel halo
+// (18 x 6 x 4 voxels) is staged in shared memory 16 channels at a time
+// (converted to BF16 and masked on the way in when the input is an FP32
+// gradient); K then runs over the 27 taps of that channel chunk, the A
+// fragments coming from shared memory and the B fragments (weights) from L1.
+// Voxels are padded to 24 BF16 in shared memory so that the eight voxel rows
+// of a fragment load fall in distinct banks.
+constexpr int CT_X = 16, CT_Y = 4, CT_Z = 2;
+constexpr int CH_X = CT_X + 2, CH_Y = CT_Y + 2, CH_Z = CT_Z + 2;
+constexpr int CH_VOX = CH_X * CH_Y * CH_Z;
+constexpr int CH_PITCH = 24;
+
 template <bool F32, int NT>
-__global__ void __launch_bounds__(128) k_conv(const ConvArgs a) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-    const long long m0 = (long long)warp * 16;
-    if (m0 >= a.nvox) return;
-    const int Cin = a.C1 + a.C2;
-    long long vrow[2];
-    int cz[2], cy[2], cx[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const long long v = m0 + g + 8 * h;
-        vrow[h] = v < a.nvox ? v : -1;
-        const long long vv = v < a.nvox ? v : 0;
-        cx[h] = (int)(vv % a.X);
-        cy[h] = (int)((vv / a.X) % a.Y);
-        cz[h] = (int)(vv / ((long long)a.X * a.Y));
-    }
+__global__ void __launch_bounds__(256) k_conv(const ConvArgs a, int tiles_x, int tiles_y) {
+    __shared__ __align__(16) bf16 sx[CH_VOX * CH_PITCH];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, q = lane & 3;
+    int blk = blockIdx.x;
+    const int tx = blk % tiles_x;
+    blk /= tiles_x;
+    const int ty = blk % tiles_y, tz = blk / tiles_y;
+    const int x0 = tx * CT_X, y0 = ty * CT_Y, z0 = tz * CT_Z;
+    const int wy = warp % CT_Y, wz = warp / CT_Y;
+    const int Cin = a.C1 + a.C2, nchunk = Cin / 16;
     float acc[NT][4];
 #pragma unroll
     for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-    for (int tap = 0; tap < 27; ++tap) {
-        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        long long nb[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int z = cz[h] + dz, y = cy[h] + dy, x = cx[h] + dx;
-            nb[h] = (vrow[h] >= 0 && z >= 0 && z < a.Z && y >= 0 && y < a.Y && x >= 0 && x < a.X)
-                        ? x + (long long)a.X * (y + (long long)a.Y * z)
-                        : -1;
+    for (int chunk = 0; chunk < nchunk; ++chunk) {
+        const int k0 = chunk * 16;
+        const bool first = k0 < a.C1;
+        const void* src = first ? a.in1 : a.in2;
+        const int cs = first ? a.C1 : a.C2;
+        const int kk = first ? k0 : k0 - a.C1;
+        const bf16* mk = first ? a.mask1 : nullptr;
+        __syncthreads();
+        for (int i = tid; i < CH_VOX * 2; i += 256) {
+            const int vox = i >> 1, h = i & 1;
+            const int hx = vox % CH_X, hy = (vox / CH_X) % CH_Y, hz = vox / (CH_X * CH_Y);
+            const int x = x0 - 1 + hx, y = y0 - 1 + hy, z = z0 - 1 + hz;
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (x >= 0 && x < a.X && y >= 0 && y < a.Y && z >= 0 && z < a.Z) {
+                const long long off = (x + (long long)a.X * (y + (long long)a.Y * z)) * cs + kk + 8 * h;
+                if (F32) {
+                    const float4 f0 = *reinterpret_cast<const float4*>((const float*)src + off);
+                    const float4 f1 = *reinterpret_cast<const float4*>((const float*)src + off + 4);
+                    val = make_uint4(pack_bf16(f0.x, f0.y), pack_bf16(f0.z, f0.w),
+                                     pack_bf16(f1.x, f1.y), pack_bf16(f1.z, f1.w));
+                } else {
+                    val = *reinterpret_cast<const uint4*>((const bf16*)src + off);
+                }
+                if (mk) {
+                    const uint4 m = *reinterpret_cast<const uint4*>(mk + off);
+                    val = make_uint4(mask_pair(val.x, m.x), mask_pair(val.y, m.y),
+                                     mask_pair(val.z, m.z), mask_pair(val.w, m.w));
+                }
+            }
+            *reinterpret_cast<uint4*>(sx + vox * CH_PITCH + 8 * h) = val;
         }
-        const bf16* Wt = a.W + (size_t)tap * a.Cout * Cin;
-        for (int k0 = 0; k0 < Cin; k0 += 16) {
-            const bool first = k0 < a.C1;
-            const void* src = first ? a.in1 : a.in2;
-            const int cs = first ? a.C1 : a.C2;
-            const int kk = first ? k0 : k0 - a.C1;
-            const bf16* mk = first ? a.mask1 : nullptr;
+        __syncthreads();
+        const bf16* Wc = a.W + k0 + 2 * q;
+#pragma unroll 3
+        for (int tap = 0; tap < 27; ++tap) {
+            const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+            const bf16* p0 = sx + (((wz + dz) * CH_Y + (wy + dy)) * CH_X + (g + dx)) * CH_PITCH + 2 * q;
+            const bf16* p1 = p0 + 8 * CH_PITCH;
             uint32_t af[4];
-            af[0] = load_pair<F32>(src, nb[0], cs, kk + 2 * q, mk, cs);
-            af[1] = load_pair<F32>(src, nb[1], cs, kk + 2 * q, mk, cs);
-            af[2] = load_pair<F32>(src, nb[0], cs, kk + 2 * q + 8, mk, cs);
-            af[3] = load_pair<F32>(src, nb[1], cs, kk + 2 * q + 8, mk, cs);
+            af[0] = *reinterpret_cast<const uint32_t*>(p0);
+            af[1] = *reinterpret_cast<const uint32_t*>(p1);
+            af[2] = *reinterpret_cast<const uint32_t*>(p0 + 8);
+            af[3] = *reinterpret_cast<const uint32_t*>(p1 + 8);
+            const bf16* Wt = Wc + (size_t)tap * a.Cout * Cin;
 #pragma unroll
             for (int n = 0; n < NT; ++n) {
-                const bf16* wrow = Wt + (size_t)(n * 8 + g) * Cin + k0 + 2 * q;
+                const bf16* wrow = Wt + (size_t)(n * 8 + g) * Cin;
                 const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wrow);
                 const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wrow + 8);
                 mma16816(acc[n], af, b0, b1);
             }
         }
     }
+    const int y = y0 + wy, z = z0 + wz;
+    if (y >= a.Y || z >= a.Z) return;
 #pragma unroll
-    for (int n = 0; n < NT; ++n)
+    for (int h = 0; h < 2; ++h) {
+        const int x = x0 + g + 8 * h;
+        if (x >= a.X) continue;
+        const long long v = x + (long long)a.X * (y + (long long)a.Y * z);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (vrow[h] < 0) continue;
+        for (int n = 0; n < NT; ++n) {
             const int c = n * 8 + 2 * q;
             float v0 = acc[n][2 * h], v1 = acc[n][2 * h + 1];
             if (a.bias) {
@@ -109,7 +127,7 @@ __global__ void __launch_bounds__(128) k_conv(const ConvArgs a) {
                 v0 = fmaxf(v0, 0.f);
                 v1 = fmaxf(v1, 0.f);
             }
-            const long long o = vrow[h] * a.out_cstride + a.out_coff + c;
+            const long long o = v * a.out_cstride + a.out_coff + c;
             if (a.out_b) {
                 *reinterpret_cast<uint32_t*>(a.out_b + o) = pack_bf16(v0, v1);
             } else if (a.accumulate) {
@@ -120,16 +138,18 @@ __global__ void __launch_bounds__(128) k_conv(const ConvArgs a) {
                 a.out_f[o + 1] = v1;
             }
         }
+    }
 }
 
 void conv_forward(const ConvArgs& a, bool in_fp32, cudaStream_t s) {
-    const long long warps = (a.nvox + 15) / 16;
-    const unsigned blocks = (unsigned)((warps + 3) / 4);
+    const int tiles_x = (a.X + CT_X - 1) / CT_X, tiles_y = (a.Y + CT_Y - 1) / CT_Y;
+    const int tiles_z = (a.Z + CT_Z - 1) / CT_Z;
+    const unsigned blocks = (unsigned)((long long)tiles_x * tiles_y * tiles_z);
     const int nt = a.Cout / 8;
 #define TO3D_CONV(NTV)                                                              \
     if (nt == NTV) {                                                                \
-        if (in_fp32) k_conv<true, NTV><<<blocks, 128, 0, s>>>(a);                   \
-        else k_conv<false, NTV><<<blocks, 128, 0, s>>>(a);                          \
+        if (in_fp32) k_conv<true, NTV><<<blocks, 256, 0, s>>>(a, tiles_x, tiles_y);  \
+        else k_conv<false, NTV><<<blocks, 256, 0, s>>>(a, tiles_x, tiles_y);         \
         return;                                                                     \
     }
     TO3D_CONV(1) TO3D_CONV(2) TO3D_CONV(4) TO3D_CONV(6) TO3D_CONV(8) TO3D_CONV(12) TO3D_CONV(16)
