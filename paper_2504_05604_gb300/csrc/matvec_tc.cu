@@ -39,7 +39,12 @@
 // once per CTA.  Clamped dofs hold r = p = 0 in the inner solve, so the
 // kernel needs no mask; the update kernel masks q.
 //
-// Operand formats (prec):
+// Every element vector is taken relative to its local node 0 before it is
+// rounded (p_e - t_e with t_e the node-0 displacement repeated: KE t_e = 0),
+// so the 16-bit rounding and the FP32 accumulation act on differences, which
+// for the smooth fields of the slow CG modes are far smaller than the values.
+//
+// Operand formats (prec), applied to those differences:
 //   1  BF16:    A = bf16(p_e)
 //   2  BF16X2:  A_hi = bf16(p_e), A_lo = bf16(p_e - A_hi); D accumulates both
 //   3  FP16:    p_e scaled by a power of two so max|p_e| lies in [2^10, 2^11)
@@ -422,6 +427,14 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
                     v[3 * bb + 1] = src[TC_PLANE];
                     v[3 * bb + 2] = src[2 * TC_PLANE];
                 }
+                // KE annihilates rigid translations, so the element vector
+                // may be taken relative to its local node 0: for smooth
+                // fields the differences are much smaller than the values,
+                // and so are their 16-bit rounding and the FP32 accumulation
+                // errors (the product itself is unchanged)
+#pragma unroll
+                for (int i = 3; i < 24; ++i) v[i] -= v[i % 3];
+                v[0] = v[1] = v[2] = 0.f;
                 float code = 0.f;
                 if (SCALED) {
                     float m = 0.f;

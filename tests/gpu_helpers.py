@@ -35,7 +35,9 @@ def bf16_round(a32):
 
 
 def emulate_lowp(prob, x, p32, prec):
-    """y = Kbar p with the operand rounding of the tensor-core forms, in FP64."""
+    """y = Kbar p with the operand rounding of the tensor-core forms, in FP64:
+    element vectors taken relative to their local node 0, then rounded as
+    the form prescribes."""
     nelx, nely, nelz = prob.nelx, prob.nely, prob.nelz
     KE = fem.element_stiffness(prob.nu)
     E = fem.simp_modulus(x, prob.penal, prob.E0, prob.Emin)
@@ -43,6 +45,9 @@ def emulate_lowp(prob, x, p32, prec):
     fixed = prob.fixed != 0
     q = np.where(fixed, np.float32(0), p32.astype(np.float32))
     pe = q[ed]                                       # float32 [nel, 24]
+    # the kernel takes each element vector relative to its local node 0
+    # (KE annihilates translations), in FP32, before any rounding
+    pe = (pe - np.tile(pe[:, 0:3], (1, 8))).astype(np.float32)
     if prec == 1:
         pe = bf16_round(pe).astype(np.float64)
     elif prec == 2:
