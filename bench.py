@@ -43,7 +43,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", type=int, default=2, help="0 fp64, 1 bf16, 2 bf16x2, 3 fp16")
+    ap.add_argument("--precision", type=int, default=1,
+                    help="0 fp64, 1 bf16, 2 bf16 hi+lo, 3 fp16, 4 fp16 hi+lo (tensor-core forms "
+                         "with FP64 defect correction)")
     ap.add_argument("--size", default="480x160x80")
     ap.add_argument("--workload", default="large", choices=["large", "batched64"],
                     help="large: the 480x160x80 cantilever; batched64: 64 seeded uneven "
@@ -206,11 +208,10 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------------ GPU arm
-# DRAM bytes (read + write) of one launch of the fused BF16 hi+lo tensor-core
-# kernel at 480x160x80 from one ncu capture of the current kernel
-# (profiles/k_matvec_tc_bf16x2_480x160x80.md); reported only for that form
-# and size.
-TC_TRAFFIC_BYTES = {(2, 480, 160, 80): 232_763_904 + 130_060_032}
+# DRAM bytes (read + write) of one launch of the fused tensor-core kernel at
+# 480x160x80 from one ncu capture of the current kernel (profiles/); reported
+# only for the forms and size captured.
+TC_TRAFFIC_BYTES = {}
 
 
 def max_over_ranks(x: float, device) -> float:
