@@ -351,7 +351,7 @@ def test_trained_network_beats_jacobi_on_a_new_design(trained):
 
 
 def test_flexible_cg_solves_to_tolerance(trained):
-    """The learned solve is judged by the true FP64 residual, with the
+    """The learned solve is decided by the true FP64 residual, with the
     Jacobi-PCG fallback finishing it if the network stalls; the iteration
     counts against plain Jacobi-PCG are printed (what the trained network
     gains inside the solver)."""
