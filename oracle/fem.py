@@ -148,6 +148,39 @@ def matvec_elementwise(nelx, nely, nelz, E, KE, p, fixed) -> np.ndarray:
     return np.where(fixed != 0, p, y)
 
 
+def matvec_rows(nelx, nely, nelz, E, KE, p, fixed, rows, absolute=False):
+    """Selected entries y[rows] of y = Kbar p (``matvec_elementwise``), each
+    summed over the (at most 8) elements around its node; with `absolute`,
+    the same sums of |E_e KE_ij p_j| (the size of the terms being summed).
+    For grids too large to assemble."""
+    nx, ny = nelx + 1, nely + 1
+    out = np.zeros(len(rows))
+    for t, d in enumerate(rows):
+        if fixed[d]:
+            out[t] = abs(p[d]) if absolute else p[d]
+            continue
+        node, comp = divmod(int(d), 3)
+        i, j, k = node % nx, (node // nx) % ny, node // (nx * ny)
+        acc = 0.0
+        for c in (0, 1):
+            for b in (0, 1):
+                for a in (0, 1):
+                    ei, ej, ek = i - a, j - b, k - c
+                    if not (0 <= ei < nelx and 0 <= ej < nely and 0 <= ek < nelz):
+                        continue
+                    e = ei + nelx * (ej + nely * ek)
+                    row = KE[3 * (a + 2 * b + 4 * c) + comp]
+                    for m, (aa, bb, cc) in enumerate(_corners().astype(int)):
+                        nd = (ei + aa) + nx * ((ej + bb) + ny * (ek + cc))
+                        for cm in range(3):
+                            dof = 3 * nd + cm
+                            v = 0.0 if fixed[dof] else p[dof]
+                            term = E[e] * row[3 * m + cm] * v
+                            acc += abs(term) if absolute else term
+        out[t] = acc
+    return out
+
+
 def masked_load(f: np.ndarray, fixed: np.ndarray) -> np.ndarray:
     return np.where(fixed != 0, 0.0, f)
 
