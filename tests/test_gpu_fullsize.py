@@ -86,5 +86,8 @@ def test_full_size_oc_iteration_properties(big):
     ed = np.stack([3 * ((i + a) + nx * ((j + b) + ny * (k + c))) + comp
                    for (a, b, c) in corner for comp in range(3)], axis=1)
     ce_ref = np.einsum("ei,ij,ej->e", u[ed], KE, u[ed])
-    assert np.allclose(ce[els], ce_ref, rtol=1e-12, atol=1e-12 * np.abs(ce_ref).max())
+    # the physical u is smooth: u_e^T KE u_e cancels heavily (rigid parts),
+    # so rounding is bounded by the sum of |terms|, not by ce itself
+    ab = np.einsum("ei,ij,ej->e", np.abs(u[ed]), np.abs(KE), np.abs(u[ed]))
+    assert np.all(np.abs(ce[els] - ce_ref) <= 1e-13 * ab + 1e-300)
     ctx.close()
