@@ -484,7 +484,9 @@ def batched(args):
     from synth import problems
 
     probs = problems.config_batched(64)
-    prec = args.precision if args.precision != 0 else 2
+    # the two-slice operand: on these small, void-riddled grids the single-
+    # slice one stalls the device-side defect correction of some problems
+    prec = args.precision if args.precision in (2, 4) else 2
     stream = torch.cuda.current_stream()
     b = Batch(probs, precision=prec, inner_rtol=args.inner_rtol)
     for _ in range(args.warmup):

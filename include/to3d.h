@@ -63,9 +63,11 @@ typedef enum {
  * FP64 dot products and norms, u += d in FP64. */
 typedef enum {
     TO3D_F64 = 0,        /* FP64 Jacobi-PCG with the FP64 element matvec      */
-    TO3D_BF16_DC = 1,    /* BF16 operand (one slice)                          */
+    TO3D_BF16_DC = 1,    /* BF16 operand (one slice); after 8 outer stalls in a
+                          * solve it switches to the two-slice form           */
     TO3D_BF16X2_DC = 2,  /* BF16 hi + lo slices (about 16 mantissa bits)      */
-    TO3D_FP16_DC = 3,    /* FP16 operand with per-element power-of-two scale  */
+    TO3D_FP16_DC = 3,    /* FP16 operand with per-element power-of-two scale
+                          * (same escalation to two slices)                   */
     TO3D_FP16X2_DC = 4   /* scaled FP16 hi + lo slices (about 22 bits)        */
 } to3d_precision;
 
@@ -302,7 +304,9 @@ typedef struct to3d_batch to3d_batch;
  * and bisection loops run on the device (conditional graph nodes); the
  * tensor-core kernel's z-segment length is autotuned per grid shape.  Only
  * the tensor-core defect-correction precisions are accepted (EINVAL for
- * TO3D_F64).  `stream`: the caller's stream that each step is ordered on. */
+ * TO3D_F64); the device-side solver has no single- to two-slice escalation,
+ * so the two-slice forms are the robust choice here (a single-slice solve
+ * that stalls ends in TO3D_ENOCONV).  `stream`: the caller's stream that each step is ordered on. */
 TO3D_API to3d_status to3d_batch_create(int32_t nprob, const to3d_params* params,
                                        const uint8_t* const* fixed, const double* const* load,
                                        const uint8_t* const* passive, void* stream,

@@ -268,11 +268,6 @@ static to3d_status pcg32_chunk(to3d_ctx* c, int prec, int n) {
     if (n == c->chunk) {
         if (!c->g_pcg32 || c->g_pcg32_prec != prec) {
             if (c->g_pcg32) cudaGraphExecDestroy(c->g_pcg32);
-    if (c->g_iter) cudaGraphExecDestroy(c->g_iter);
-    if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
-    if (c->cap_stream3) cudaStreamDestroy(c->cap_stream3);
-    if (c->dcctl) cudaFree(c->dcctl);
-    if (c->dcctl_h) cudaFreeHost(c->dcctl_h);
             c->g_pcg32 = nullptr;
             cudaGraph_t gr;
             CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -356,12 +351,17 @@ static to3d_status solve_f64(to3d_ctx* c, const double* f, double fnorm, to3d_so
 // has dropped by the factor delta (= inner_rtol) since the last replacement,
 // u absorbs the correction d in FP64, the true residual f - K u is formed in
 // FP64 and replaces the FP32 residual, and the CG continues from its last
-// search direction, re-orthogonalised against the new residual.  The solve
-// ends when the true relative residual is <= cg_rtol.
+// search direction, re-orthogonalised against the new residual.  When the
+// true residual does not halve over a segment the inner CG restarts from it;
+// after 8 such stalls a single-slice operand form switches to its two-slice
+// form for the rest of the solve.  The solve ends when the true relative
+// residual is <= cg_rtol.
+constexpr int kEscalateAfterStalls = 8;
+
 static to3d_status solve_dc(to3d_ctx* c, const double* f, double fnorm, to3d_solve_info* info) {
     const double tol = c->prm.cg_rtol;
     const double delta = c->prm.inner_rtol;
-    const int prec = c->prm.precision;
+    int prec = c->prm.precision;
     const long long ndof = 3 * c->g.nnode;
     int total = 0, outer = 0, status = TO3D_OK, stalls = 0;
     double relres = 0.0;
@@ -413,6 +413,14 @@ static to3d_status solve_dc(to3d_ctx* c, const double* f, double fnorm, to3d_sol
                 if (++stalls > 50) {
                     status = TO3D_ENOCONV;
                     break;
+                }
+                // a single-slice operand that keeps stalling the outer
+                // iteration is too coarse for this system: finish the solve
+                // with the two-slice form of the same format
+                if (stalls == kEscalateAfterStalls && (prec == TO3D_BF16_DC || prec == TO3D_FP16_DC)) {
+                    prec += 1;
+                    if (c->trace)
+                        std::fprintf(stderr, "to3d: %d stalls, inner operand now form %d\n", stalls, prec);
                 }
                 launch_ss_reset(c, c->stream,
                                 std::fmax(delta * delta * (double)ndof * (relres / relres0) *
