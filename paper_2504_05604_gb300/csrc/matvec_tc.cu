@@ -65,7 +65,6 @@ constexpr int TC_BX = 15, TC_BY = 7;                 // owned nodes per layer
 constexpr int TC_EX = TC_BX + 1, TC_EY = TC_BY + 1;  // elements per layer (16 x 8)
 constexpr int TC_PY = TC_BY + 2;                     // node rows per stage (9)
 constexpr int TC_BOXX = 20;                          // nodes per stage row (17 needed + shift)
-constexpr int TC_NS = 7;                             // ring stages
 constexpr int TC_PLANE = TC_BOXX * TC_PY;            // 180 nodes per stage plane
 constexpr int TC_VEC_BYTES = 3 * TC_PLANE * 4;       // one 3-component box (2160 B)
 constexpr int TC_STAGE_R = 0;                        // byte offsets inside a stage
