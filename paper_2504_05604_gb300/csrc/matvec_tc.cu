@@ -15,30 +15,30 @@
 // multiple of 4, so every node row starts on a 16-byte boundary and a TMA
 // box can start at any multiple of 4 nodes.  Pad nodes hold zeros.
 //
-// Work decomposition.  A CTA owns a 15 x 7 column of nodes over a segment of
-// LZ node layers and walks up it one element layer at a time (16 x 8 = 128
-// elements: one M = 128 MMA).  Node layers arrive by TMA into a 7-stage ring
-// (r, p_old and M^-1 boxes of 20 x 9 nodes, all three components), issued
-// by one thread several layers ahead and completed on per-stage mbarriers.
-// Per element layer l:
-//   (f) node layer l+2 is waited for and turned in place into the new search
-//       direction p_new = M^-1 r + beta p_old (plain mode: p itself); owned
-//       nodes of p_new go to global memory;
-//   (a) every thread gathers its element's 24 values from two ring stages,
-//       rounds them to the 16-bit operand format and writes one A row;
-//   (c) one thread issues the MMAs into one of two TMEM accumulators (the
-//       MMA of layer l overlaps the epilogue of layer l-1) and refills the
-//       ring stage that the previous node layers no longer need;
-//   (d) the epilogue scales each element row by E_e and stores it to shared
-//       memory; (e) one thread per owned node sums the four in-layer element
-//       contributions of the node layer below (c = 0) and carries the c = 1
-//       halves in registers to the next node layer.
+// Work decomposition.  A persistent grid of 3 CTAs per SM; a CTA owns a
+// 15 x 7 column of nodes over a segment of LZ node layers and walks up it
+// one element layer at a time (16 x 8 = 128 elements: one M = 128 MMA).
+// Node layers arrive by TMA into a ring of 6 or 7 stages (r, p_old and M^-1
+// boxes of 20 x 9 nodes, all three components, plus the layer's moduli).
+// Warp roles (details at TC_ROLE_THREADS):
+//   TMA warp      issues the loads several layers ahead;
+//   builder warps turn each node layer in place into the new search
+//                 direction p_new = zcoef M^-1 r + beta p_old (plain mode: p
+//                 itself), store the 16-byte chunks of owned node rows of
+//                 p_new, gather each element's 24 values from two ring
+//                 stages and write one A row in the operand format;
+//   MMA warp      issues the MMAs into one of four TMEM accumulators;
+//   epilogue      reads TMEM, scales each element row by E_e, assembles the
+//                 nodes through warp shuffles and one shared-memory exchange
+//                 per layer, carries the upper halves to the next layer in
+//                 registers, stores q once per owned node and accumulates
+//                 p_new^T q.
 // Every node is written once, by the CTA that owns it, with a plain store:
-// no atomics, no zero fill of y, deterministic results.  The grid is
-// persistent, so TMEM allocation, barrier set-up and the B tile load happen
-// once per CTA.  Clamped dofs hold r = p = 0 in the inner solve, so the
-// kernel needs no mask; the update kernel masks q.
-//
+// no atomics, no zero fill of y, deterministic results.  TMEM allocation,
+// barrier set-up and the B tile load happen once per CTA.  Clamped dofs hold
+// r = p = 0 in the inner solve, so the kernel needs no mask; the update
+// kernel masks q.
+
 // Every element vector is taken relative to its local node 0 before it is
 // rounded (p_e - t_e with t_e the node-0 displacement repeated: KE t_e = 0),
 // so the 16-bit rounding and the FP32 accumulation act on differences, which
