@@ -155,7 +155,11 @@ TO3D_API to3d_status to3d_kernel_stats(to3d_ctx* ctx, int32_t which, double* ms_
                                        int64_t* samples, int32_t reset);
 
 /* One OC iteration (Section 2.5): solve K(x) u = f, element energies and
- * sensitivities, filter, OC update of x.  `info` may be NULL. */
+ * sensitivities, filter, OC update of x.  With params.filter =
+ * TO3D_FILTER_DENS (Section 2.4, density filter) the analysis runs on
+ * xphys = H x / Hs with passive elements pinned, the sensitivities are
+ * carried back by H^T (dc / Hs), and the OC update and its volume act on x.
+ * `info` may be NULL. */
 TO3D_API to3d_status to3d_step(to3d_ctx* ctx, to3d_iter_info* info);
 /* `iters` OC iterations; hist [iters] may be NULL. */
 TO3D_API to3d_status to3d_run(to3d_ctx* ctx, int32_t iters, to3d_iter_info* hist);
@@ -304,7 +308,8 @@ typedef struct to3d_batch to3d_batch;
  * and bisection loops run on the device (conditional graph nodes); the
  * tensor-core kernel's z-segment length is autotuned per grid shape.  Only
  * the tensor-core defect-correction precisions are accepted (EINVAL for
- * TO3D_F64); the device-side solver has no single- to two-slice escalation,
+ * TO3D_F64) with the sensitivity filter (EINVAL for TO3D_FILTER_DENS); the
+ * device-side solver has no single- to two-slice escalation,
  * so the two-slice forms are the robust choice here (a single-slice solve
  * that stalls ends in TO3D_ENOCONV).  `stream`: the caller's stream that each step is ordered on. */
 TO3D_API to3d_status to3d_batch_create(int32_t nprob, const to3d_params* params,

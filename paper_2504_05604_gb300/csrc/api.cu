@@ -151,6 +151,7 @@ static cudaError_t dalloc(T** p, size_t n) {
 }
 
 static void free_all(to3d_ctx* c) {
+    if (c->xphys) cudaFree(c->xphys);
     void* ptrs[] = {c->x, c->xnew, c->E, c->E32, c->ce, c->dc, c->dcf, c->Hs, c->ocq, c->oclo,
                     c->ochi, c->passive, c->nodemask, c->dinv, c->dinv32, c->f, c->ftmp, c->u,
                     c->r, c->p, c->q, c->tmp, c->d32, c->r32, c->p32a, c->p32b, c->q32,
@@ -872,19 +873,30 @@ to3d_status to3d_oc_update(to3d_ctx* c, const double* x, const double* dcf, doub
 
 to3d_status to3d_step(to3d_ctx* c, to3d_iter_info* info) {
     if (!c) return TO3D_EINVAL;
-    if (c->prm.filter != TO3D_FILTER_SENS)
-        return set_err(c, TO3D_EINVAL, "the OC step supports the sensitivity filter");
     cudaStream_t s = c->stream;
     to3d_status st;
+    // density filter (Section 2.4): the analysis runs on the filtered field
+    // xphys = H x / Hs (passive elements pinned), and the chain rule carries
+    // its sensitivities back, dc_x = H^T (dc / Hs); the OC update acts on x
+    const bool dens = c->prm.filter == TO3D_FILTER_DENS;
+    if (dens && !c->xphys && cudaMalloc(&c->xphys, sizeof(double) * c->g.nel) != cudaSuccess)
+        return set_err(c, TO3D_ENOMEM, "filtered densities");
+    const double* xa = dens ? c->xphys : c->x;
     CK(cudaEventRecord(c->ev[0], s));
-    if ((st = prepare_operator(c, c->x))) return st;
+    if (dens) {
+        launch_filter(c, s, 1, c->x, nullptr, c->xphys);
+        launch_pin_passive(c, s, c->xphys);
+        LK("density filter");
+    }
+    if ((st = prepare_operator(c, xa))) return st;
     to3d_solve_info si{};
     if ((st = solve_current(c, c->f, c->fnorm, &si))) return st;
     CK(cudaEventRecord(c->ev[1], s));
-    launch_sensitivity(c, s, c->x, c->u, c->ce, c->dc);
+    launch_sensitivity(c, s, xa, c->u, c->ce, c->dc);
     LK("sensitivity");
     CK(cudaEventRecord(c->ev[2], s));
-    launch_filter(c, s, 0, c->x, c->dc, c->dcf);
+    if (dens) launch_filter(c, s, 2, c->dc, nullptr, c->dcf);
+    else launch_filter(c, s, 0, c->x, c->dc, c->dcf);
     LK("filter");
     CK(cudaEventRecord(c->ev[3], s));
     const double target = c->prm.volfrac * (double)c->ndesign;

@@ -335,8 +335,10 @@ to3d_status to3d_batch_create(int32_t nprob, const to3d_params* params, const ui
     if (!out) return TO3D_EINVAL;
     *out = nullptr;
     if (nprob < 1 || !params || !fixed || !load) return TO3D_EINVAL;
-    for (int i = 0; i < nprob; ++i)
+    for (int i = 0; i < nprob; ++i) {
         if (params[i].precision == TO3D_F64) return TO3D_EINVAL;   // tensor-core forms only
+        if (params[i].filter != TO3D_FILTER_SENS) return TO3D_EINVAL;   // sensitivity filter only
+    }
     to3d_batch* b = new (std::nothrow) to3d_batch();
     if (!b) return TO3D_ENOMEM;
     b->stream = (cudaStream_t)stream;

@@ -266,6 +266,22 @@ void launch_sensitivity_raw(const KE64& ke, const Grid& g, cudaStream_t s, const
                                                           comp_out);
 }
 
+// passive elements keep their pinned density: void 0, solid 1
+__global__ void k_pin_passive(long long nel, const uint8_t* __restrict__ passive,
+                              double* __restrict__ x) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= nel) return;
+    const uint8_t t = passive[e];
+    if (t == 1) x[e] = 0.0;
+    else if (t == 2) x[e] = 1.0;
+}
+
+void launch_pin_passive(to3d_ctx* c, cudaStream_t s, double* x) {
+    if (!c->passive) return;
+    k_pin_passive<<<el_blocks(c->g.nel), EL_THREADS, 0, s>>>(c->g.nel, c->passive, x);
+    c->launches++;
+}
+
 void launch_hs(to3d_ctx* c, cudaStream_t s) {
     k_hs<<<el_blocks(c->g.nel), EL_THREADS, 0, s>>>(*c->st, c->g, c->Hs);
     c->launches++;

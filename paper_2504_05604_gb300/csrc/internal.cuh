@@ -87,6 +87,7 @@ struct to3d_ctx {
     bool have_u = false;
     int pcg_its_est = 0;           // iterations of the last FP64 Jacobi-PCG solve (0: none yet)
     const double* xop = nullptr;   // densities the operator was last prepared for (device)
+    double* xphys = nullptr;       // filtered densities of the density-filter OC step
     bool have_dinv = false;
 
     to3d::KE64 ke;                        // unit-modulus element stiffness
@@ -196,6 +197,7 @@ void init_tc_attributes();
 bool prepare_tc_operands(to3d_ctx* c);
 
 // element.cu
+void launch_pin_passive(to3d_ctx* c, cudaStream_t s, double* x);
 void launch_sensitivity(to3d_ctx* c, cudaStream_t s, const double* x, const double* u,
                         double* ce, double* dc);
 void launch_hs(to3d_ctx* c, cudaStream_t s);
