@@ -30,11 +30,12 @@ if ROOT not in sys.path:
 METRIC = "OC iters/s at 480x160x80, chosen vs plain FP64 Jacobi-PCG at rel.res 1e-8"
 UNIT = "OC iters/s"
 PREC_NAMES = {0: "fp64", 1: "bf16-dc", 2: "bf16x2-dc", 3: "fp16-dc", 4: "fp16x2-dc"}
-# Jacobi-PCG iterations per OC iteration used to turn the oracle's measured
-# per-iteration cost into OC iterations/s when no GPU run in the same process
-# supplies the count (reference arm): the mean CG iteration count of OC
-# iterations 4-13 at 480x160x80 measured on GB300 with this library.
-REF_ITERS_PER_OC = 3000
+# FP64 Jacobi-PCG iterations per OC iteration, used to turn the oracle's
+# measured per-iteration cost into OC iterations/s when no GPU run in the
+# same process supplies the count (reference arm): the library's FP64 form
+# at 480x160x80 needs 5116 iterations from the design after OC iteration 5
+# and 6321 from the one after iteration 10; about 5700 over iterations 4-11.
+REF_ITERS_PER_OC = 5700
 
 
 def parse():
@@ -181,6 +182,16 @@ def run_cpu_leg_subprocess(args, its):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def workload_config(args, world):
+    """The `config` object both arms print."""
+    return {"workload": f"cantilever {args.size}, centre load on x=nelx face, volfrac 0.2, "
+                        f"rmin 2.5, penal 3, OC iterations {args.warmup + 1}-"
+                        f"{args.warmup + args.steps} from x0 = volfrac",
+            "solver_rtol": 1e-8,
+            "l2": "working set (>1 GB) larger than L2; no flush needed",
+            "parallelism": f"replicas x{world}"}
+
+
 def reference_arm(args):
     """The oracle as the reference arm: each step is one bounded sample."""
     rank = int(os.environ.get("RANK", "0"))
@@ -199,8 +210,8 @@ def reference_arm(args):
             "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": f"cantilever {args.size}, centre load, volfrac 0.2, rmin 2.5",
-                       "sample": "bounded (see cpu_baseline)"},
+            "config": dict(workload_config(args, 1), form="fp64 oracle (CPU)",
+                           sample="bounded (see cpu_baseline)"),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                              "sample": r["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -441,19 +452,16 @@ def ours(args):
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
     cpu = None
     if not args.no_cpu and world == 1:
-        cpu = run_cpu_leg_subprocess(args, statistics.mean(its))
+        # the oracle solves with FP64 Jacobi-PCG: its iteration count is the
+        # plain FP64 form's, measured above when that leg ran
+        cpu = run_cpu_leg_subprocess(args, fp64["cg_iters"] if fp64 else REF_ITERS_PER_OC)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16 operands, f32 inner CG, f64 defect correction" if args.precision else "f64",
         "data": "synthetic",
-        "config": {"workload": f"cantilever {args.size}, centre load on x=nelx face, volfrac 0.2, "
-                               f"rmin 2.5, penal 3, OC iterations {args.warmup + 1}-"
-                               f"{args.warmup + args.steps} from x0 = volfrac",
-                   "form": PREC_NAMES[args.precision], "solver_rtol": 1e-8,
-                   "l2": "working set (>1 GB) larger than L2; no flush needed",
-                   "parallelism": f"replicas x{world}"},
+        "config": dict(workload_config(args, world), form=PREC_NAMES[args.precision]),
         "gpu_launches": int(launches),
         "status": int(status),
         "cg_iters_per_step": its,
