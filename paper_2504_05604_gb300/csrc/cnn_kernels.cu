@@ -27,22 +27,25 @@ __device__ __forceinline__ uint32_t mask_pair(uint32_t v, uint32_t m) {
     return v & (keep_lo | keep_hi);
 }
 
-// Implicit-GEMM 3x3x3 convolution.  A block computes a 16 x 4 x 2 tile of
-// output voxels (8 warps, one 16-voxel x-row each: the M = 16 rows of the
-// MMA) for all output channels.  The input tile with its one-voxel halo
-// (18 x 6 x 4 voxels) is staged in shared memory 16 channels at a time
-// (converted to BF16 and masked on the way in when the input is an FP32
-// gradient); K then runs over the 27 taps of that channel chunk, the A
-// fragments coming from shared memory and the B fragments (weights) from L1.
-// Voxels are padded to 24 BF16 in shared memory so that the eight voxel rows
-// of a fragment load fall in distinct banks.
-constexpr int CT_X = 16, CT_Y = 4, CT_Z = 2;
-constexpr int CH_X = CT_X + 2, CH_Y = CT_Y + 2, CH_Z = CT_Z + 2;
-constexpr int CH_VOX = CH_X * CH_Y * CH_Z;
+// Implicit-GEMM 3x3x3 convolution.  A block computes a 16 x 4R x 2 tile of
+// output voxels (8 warps, R 16-voxel x-rows each: the M = 16 rows of an MMA
+// per x-row) for all output channels.  The input tile with its one-voxel
+// halo (18 x (4R + 2) x 4 voxels) is staged in shared memory 16 channels at
+// a time (converted to BF16 and masked on the way in when the input is an
+// FP32 gradient); K then runs over the 27 taps of that channel chunk, the A
+// fragments coming from shared memory and the B fragments (weights) from L1,
+// each B fragment serving the warp's R rows.  Narrow layers (few output
+// channels) take R = 2 to reuse their weight fragments; wide ones R = 1 to
+// bound the accumulator registers.  Voxels are padded to 24 BF16 in shared
+// memory so that the eight voxel rows of a fragment load fall in distinct
+// banks.
+constexpr int CT_X = 16, CT_Z = 2;
+constexpr int CH_X = CT_X + 2, CH_Z = CT_Z + 2;
 constexpr int CH_PITCH = 24;
 
-template <bool F32, int NT>
+template <bool F32, int NT, int R>
 __global__ void __launch_bounds__(256) k_conv(const ConvArgs a, int tiles_x, int tiles_y) {
+    constexpr int CT_Y = 4 * R, CH_Y = CT_Y + 2, CH_VOX = CH_X * CH_Y * CH_Z;
     __shared__ __align__(16) bf16 sx[CH_VOX * CH_PITCH];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, q = lane & 3;
     int blk = blockIdx.x;
@@ -50,11 +53,13 @@ __global__ void __launch_bounds__(256) k_conv(const ConvArgs a, int tiles_x, int
     blk /= tiles_x;
     const int ty = blk % tiles_y, tz = blk / tiles_y;
     const int x0 = tx * CT_X, y0 = ty * CT_Y, z0 = tz * CT_Z;
-    const int wy = warp % CT_Y, wz = warp / CT_Y;
+    const int wy0 = (warp % 4) * R, wz = warp / 4;
     const int Cin = a.C1 + a.C2, nchunk = Cin / 16;
-    float acc[NT][4];
+    float acc[R][NT][4];
 #pragma unroll
-    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int n = 0; n < NT; ++n) acc[r][n][0] = acc[r][n][1] = acc[r][n][2] = acc[r][n][3] = 0.f;
     for (int chunk = 0; chunk < nchunk; ++chunk) {
         const int k0 = chunk * 16;
         const bool first = k0 < a.C1;
@@ -91,68 +96,80 @@ __global__ void __launch_bounds__(256) k_conv(const ConvArgs a, int tiles_x, int
 #pragma unroll 3
         for (int tap = 0; tap < 27; ++tap) {
             const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-            const bf16* p0 = sx + (((wz + dz) * CH_Y + (wy + dy)) * CH_X + (g + dx)) * CH_PITCH + 2 * q;
-            const bf16* p1 = p0 + 8 * CH_PITCH;
-            uint32_t af[4];
-            af[0] = *reinterpret_cast<const uint32_t*>(p0);
-            af[1] = *reinterpret_cast<const uint32_t*>(p1);
-            af[2] = *reinterpret_cast<const uint32_t*>(p0 + 8);
-            af[3] = *reinterpret_cast<const uint32_t*>(p1 + 8);
+            uint32_t af[R][4];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const bf16* p0 =
+                    sx + (((wz + dz) * CH_Y + (wy0 + r + dy)) * CH_X + (g + dx)) * CH_PITCH + 2 * q;
+                const bf16* p1 = p0 + 8 * CH_PITCH;
+                af[r][0] = *reinterpret_cast<const uint32_t*>(p0);
+                af[r][1] = *reinterpret_cast<const uint32_t*>(p1);
+                af[r][2] = *reinterpret_cast<const uint32_t*>(p0 + 8);
+                af[r][3] = *reinterpret_cast<const uint32_t*>(p1 + 8);
+            }
             const bf16* Wt = Wc + (size_t)tap * a.Cout * Cin;
 #pragma unroll
             for (int n = 0; n < NT; ++n) {
                 const bf16* wrow = Wt + (size_t)(n * 8 + g) * Cin;
                 const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wrow);
                 const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wrow + 8);
-                mma16816(acc[n], af, b0, b1);
+#pragma unroll
+                for (int r = 0; r < R; ++r) mma16816(acc[r][n], af[r], b0, b1);
             }
         }
     }
-    const int y = y0 + wy, z = z0 + wz;
-    if (y >= a.Y || z >= a.Z) return;
+    const int z = z0 + wz;
+    if (z >= a.Z) return;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int x = x0 + g + 8 * h;
-        if (x >= a.X) continue;
-        const long long v = x + (long long)a.X * (y + (long long)a.Y * z);
+    for (int r = 0; r < R; ++r) {
+        const int y = y0 + wy0 + r;
+        if (y >= a.Y) continue;
 #pragma unroll
-        for (int n = 0; n < NT; ++n) {
-            const int c = n * 8 + 2 * q;
-            float v0 = acc[n][2 * h], v1 = acc[n][2 * h + 1];
-            if (a.bias) {
-                v0 += a.bias[c];
-                v1 += a.bias[c + 1];
-            }
-            if (a.relu) {
-                v0 = fmaxf(v0, 0.f);
-                v1 = fmaxf(v1, 0.f);
-            }
-            const long long o = v * a.out_cstride + a.out_coff + c;
-            if (a.out_b) {
-                *reinterpret_cast<uint32_t*>(a.out_b + o) = pack_bf16(v0, v1);
-            } else if (a.accumulate) {
-                a.out_f[o] += v0;
-                a.out_f[o + 1] += v1;
-            } else {
-                a.out_f[o] = v0;
-                a.out_f[o + 1] = v1;
+        for (int h = 0; h < 2; ++h) {
+            const int x = x0 + g + 8 * h;
+            if (x >= a.X) continue;
+            const long long v = x + (long long)a.X * (y + (long long)a.Y * z);
+#pragma unroll
+            for (int n = 0; n < NT; ++n) {
+                const int c = n * 8 + 2 * q;
+                float v0 = acc[r][n][2 * h], v1 = acc[r][n][2 * h + 1];
+                if (a.bias) {
+                    v0 += a.bias[c];
+                    v1 += a.bias[c + 1];
+                }
+                if (a.relu) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                const long long o = v * a.out_cstride + a.out_coff + c;
+                if (a.out_b) {
+                    *reinterpret_cast<uint32_t*>(a.out_b + o) = pack_bf16(v0, v1);
+                } else if (a.accumulate) {
+                    a.out_f[o] += v0;
+                    a.out_f[o + 1] += v1;
+                } else {
+                    a.out_f[o] = v0;
+                    a.out_f[o + 1] = v1;
+                }
             }
         }
     }
 }
 
 void conv_forward(const ConvArgs& a, bool in_fp32, cudaStream_t s) {
-    const int tiles_x = (a.X + CT_X - 1) / CT_X, tiles_y = (a.Y + CT_Y - 1) / CT_Y;
+    const int nt = a.Cout / 8;
+    const int R = nt <= 4 ? 2 : 1;
+    const int tiles_x = (a.X + CT_X - 1) / CT_X, tiles_y = (a.Y + 4 * R - 1) / (4 * R);
     const int tiles_z = (a.Z + CT_Z - 1) / CT_Z;
     const unsigned blocks = (unsigned)((long long)tiles_x * tiles_y * tiles_z);
-    const int nt = a.Cout / 8;
-#define TO3D_CONV(NTV)                                                              \
-    if (nt == NTV) {                                                                \
-        if (in_fp32) k_conv<true, NTV><<<blocks, 256, 0, s>>>(a, tiles_x, tiles_y);  \
-        else k_conv<false, NTV><<<blocks, 256, 0, s>>>(a, tiles_x, tiles_y);         \
-        return;                                                                     \
+#define TO3D_CONV(NTV, RV)                                                              \
+    if (nt == NTV) {                                                                    \
+        if (in_fp32) k_conv<true, NTV, RV><<<blocks, 256, 0, s>>>(a, tiles_x, tiles_y);  \
+        else k_conv<false, NTV, RV><<<blocks, 256, 0, s>>>(a, tiles_x, tiles_y);         \
+        return;                                                                         \
     }
-    TO3D_CONV(1) TO3D_CONV(2) TO3D_CONV(4) TO3D_CONV(6) TO3D_CONV(8) TO3D_CONV(12) TO3D_CONV(16)
+    TO3D_CONV(1, 2) TO3D_CONV(2, 2) TO3D_CONV(4, 2) TO3D_CONV(6, 1) TO3D_CONV(8, 1)
+    TO3D_CONV(12, 1) TO3D_CONV(16, 1)
 #undef TO3D_CONV
 }
 
