@@ -35,8 +35,8 @@ __device__ __forceinline__ uint32_t mask_pair(uint32_t v, uint32_t m) {
 // FP32 gradient); K then runs over the 27 taps of that channel chunk, the A
 // fragments coming from shared memory and the B fragments (weights) from L1,
 // each B fragment serving the warp's R rows.  Narrow layers (few output
-// channels) take R = 2 to reuse their weight fragments; wide ones R = 1 to
-// bound the accumulator registers.  Voxels are padded to 24 BF16 in shared
+// channels) take R = 4 (16 channels) or 2 (32) to reuse their weight
+// fragments; wide ones R = 1 to bound the accumulator registers.  Voxels are padded to 24 BF16 in shared
 // memory so that the eight voxel rows of a fragment load fall in distinct
 // banks.
 constexpr int CT_X = 16, CT_Z = 2;
@@ -46,7 +46,8 @@ constexpr int CH_PITCH = 24;
 template <bool F32, int NT, int R>
 __global__ void __launch_bounds__(256) k_conv(const ConvArgs a, int tiles_x, int tiles_y) {
     constexpr int CT_Y = 4 * R, CH_Y = CT_Y + 2, CH_VOX = CH_X * CH_Y * CH_Z;
-    __shared__ __align__(16) bf16 sx[CH_VOX * CH_PITCH];
+    extern __shared__ __align__(16) uint8_t conv_smem[];
+    bf16* sx = reinterpret_cast<bf16*>(conv_smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, q = lane & 3;
     int blk = blockIdx.x;
     const int tx = blk % tiles_x;
@@ -156,19 +157,31 @@ __global__ void __launch_bounds__(256) k_conv(const ConvArgs a, int tiles_x, int
     }
 }
 
+template <bool F32, int NT, int R>
+static void launch_conv(const ConvArgs& a, unsigned blocks, int tiles_x, int tiles_y,
+                        cudaStream_t s) {
+    constexpr int bytes = CH_X * (4 * R + 2) * CH_Z * CH_PITCH * 2;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_conv<F32, NT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        attr = true;
+    }
+    k_conv<F32, NT, R><<<blocks, 256, bytes, s>>>(a, tiles_x, tiles_y);
+}
+
 void conv_forward(const ConvArgs& a, bool in_fp32, cudaStream_t s) {
     const int nt = a.Cout / 8;
-    const int R = nt <= 4 ? 2 : 1;
+    const int R = nt <= 2 ? 4 : (nt <= 4 ? 2 : 1);
     const int tiles_x = (a.X + CT_X - 1) / CT_X, tiles_y = (a.Y + 4 * R - 1) / (4 * R);
     const int tiles_z = (a.Z + CT_Z - 1) / CT_Z;
     const unsigned blocks = (unsigned)((long long)tiles_x * tiles_y * tiles_z);
-#define TO3D_CONV(NTV, RV)                                                              \
-    if (nt == NTV) {                                                                    \
-        if (in_fp32) k_conv<true, NTV, RV><<<blocks, 256, 0, s>>>(a, tiles_x, tiles_y);  \
-        else k_conv<false, NTV, RV><<<blocks, 256, 0, s>>>(a, tiles_x, tiles_y);         \
-        return;                                                                         \
+#define TO3D_CONV(NTV, RV)                                                         \
+    if (nt == NTV) {                                                               \
+        if (in_fp32) launch_conv<true, NTV, RV>(a, blocks, tiles_x, tiles_y, s);   \
+        else launch_conv<false, NTV, RV>(a, blocks, tiles_x, tiles_y, s);          \
+        return;                                                                    \
     }
-    TO3D_CONV(1, 2) TO3D_CONV(2, 2) TO3D_CONV(4, 2) TO3D_CONV(6, 1) TO3D_CONV(8, 1)
+    TO3D_CONV(1, 4) TO3D_CONV(2, 4) TO3D_CONV(4, 2) TO3D_CONV(6, 1) TO3D_CONV(8, 1)
     TO3D_CONV(12, 1) TO3D_CONV(16, 1)
 #undef TO3D_CONV
 }
