@@ -168,6 +168,13 @@ TO3D_API to3d_status to3d_run(to3d_ctx* ctx, int32_t iters, to3d_iter_info* hist
 TO3D_API to3d_status to3d_get_density(to3d_ctx* ctx, double* x, int32_t on_device);
 TO3D_API to3d_status to3d_set_density(to3d_ctx* ctx, const double* x, int32_t on_device);
 TO3D_API to3d_status to3d_get_displacement(to3d_ctx* ctx, double* u, int32_t on_device);
+/* Checkpoint / resume: x (set_density; host values must lie in [0, 1], else
+ * EINVAL), u (the next solve's warm start) and the OC iteration counter of
+ * a context.  A context given the x, u and iteration of another one repeats
+ * that one's next OC iteration exactly. */
+TO3D_API to3d_status to3d_set_displacement(to3d_ctx* ctx, const double* u, int32_t on_device);
+TO3D_API to3d_status to3d_get_iteration(const to3d_ctx* ctx, int32_t* iter);
+TO3D_API to3d_status to3d_set_iteration(to3d_ctx* ctx, int32_t iter);
 
 /* ---- single steps of the path (also used by the parity tests) ---------- */
 
@@ -322,6 +329,14 @@ TO3D_API to3d_status to3d_batch_step(to3d_batch* b, to3d_iter_info* info);
 TO3D_API to3d_status to3d_batch_get_density(to3d_batch* b, int32_t i, double* x, int32_t on_device);
 TO3D_API int32_t to3d_batch_size(const to3d_batch* b);
 TO3D_API void to3d_batch_destroy(to3d_batch* b);
+
+/* Failure-detection self-test: one thread waits, with the bounded
+ * suspend-and-poll loop every wait of the tensor-core kernel uses, on an
+ * mbarrier phase that nothing completes; after `polls` polls (1 .. 65536, at
+ * most ~1 us each) it gives up and *status receives TO3D_ETIMEOUT, the code
+ * the tensor-core kernel reports when one of its waits runs out.  Nothing
+ * hangs and the CUDA context stays usable.  `stream`: cudaStream_t as void*. */
+TO3D_API to3d_status to3d_selftest_wait_timeout(int32_t polls, int32_t* status, void* stream);
 
 /* Same results as to3d_sensitivity, but the library allocates nothing, and
  * no context is needed.  The paper has no counterpart: this entry point

@@ -78,6 +78,10 @@ _SIGS = {
     "to3d_get_density": (I32, [VP, VP, I32]),
     "to3d_set_density": (I32, [VP, VP, I32]),
     "to3d_get_displacement": (I32, [VP, VP, I32]),
+    "to3d_set_displacement": (I32, [VP, VP, I32]),
+    "to3d_get_iteration": (I32, [VP, C.POINTER(I32)]),
+    "to3d_set_iteration": (I32, [VP, I32]),
+    "to3d_selftest_wait_timeout": (I32, [I32, C.POINTER(I32), VP]),
     "to3d_matvec": (I32, [VP, VP, VP, VP, I32]),
     "to3d_matvec_lowp": (I32, [VP, VP, VP, VP, I32, I32]),
     "to3d_solve": (I32, [VP, VP, VP, VP, I32, C.POINTER(SolveInfo)]),
@@ -251,6 +255,28 @@ class Context:
         a = _Arg(x, np.float64)
         self._check(self.lib.to3d_set_density(self.h, a.ptr, a.dev), "set_density")
 
+    def set_displacement(self, u):
+        a = _Arg(u, np.float64)
+        self._check(self.lib.to3d_set_displacement(self.h, a.ptr, a.dev), "set_displacement")
+
+    @property
+    def iteration(self) -> int:
+        it = I32()
+        self._check(self.lib.to3d_get_iteration(self.h, C.byref(it)), "get_iteration")
+        return it.value
+
+    def save_state(self, path):
+        """Checkpoint: design, displacement and OC iteration to an .npz file."""
+        np.savez(path, x=self.density(), u=self.displacement(), iteration=self.iteration)
+
+    def load_state(self, path):
+        """Resume from ``save_state``: the next OC iteration repeats the one
+        the saved context would have run next."""
+        with np.load(path) as d:
+            self.set_density(np.ascontiguousarray(d["x"]))
+            self.set_displacement(np.ascontiguousarray(d["u"]))
+            self._check(self.lib.to3d_set_iteration(self.h, int(d["iteration"])), "set_iteration")
+
     def displacement(self, out=None):
         out = np.empty(self.ndof) if out is None else out
         a = _Arg(out, np.float64)
@@ -358,6 +384,16 @@ class Context:
         self._check(self.lib.to3d_cnn_train(self.h, nsnap, per_design, steps, lr, seed, source,
                                             C.byref(a), C.byref(b)), "cnn_train")
         return a.value, b.value
+
+
+def selftest_wait_timeout(polls: int = 256, stream=None) -> int:
+    """Status a bounded device-side wait reports when nothing completes it
+    (``to3d_selftest_wait_timeout``): TO3D_ETIMEOUT."""
+    st = I32()
+    r = load().to3d_selftest_wait_timeout(polls, C.byref(st), _stream_ptr(stream))
+    if r:
+        raise To3dError(r, "to3d_selftest_wait_timeout")
+    return st.value
 
 
 def _stream_ptr(stream):

@@ -567,6 +567,13 @@ to3d_status to3d_create(const to3d_params* prm, const uint8_t* fixed, const doub
         prm->precision > 4 || prm->filter < 0 || prm->filter > 1 || prm->fcg_ref_iters < 0)
         return TO3D_EINVAL;
     if (prm->precond != TO3D_JACOBI && prm->precond != TO3D_CNN_FCG) return TO3D_EINVAL;
+    {
+        // a NaN or Inf load would make every residual test false and end the
+        // solves "converged": reject it here
+        const long long ndof = 3LL * (prm->nelx + 1) * (prm->nely + 1) * (prm->nelz + 1);
+        for (long long d = 0; d < ndof; ++d)
+            if (!std::isfinite(load[d])) return TO3D_EINVAL;
+    }
 
     to3d_ctx* c = new (std::nothrow) to3d_ctx();
     if (!c) return TO3D_ENOMEM;
@@ -702,9 +709,34 @@ to3d_status to3d_get_density(to3d_ctx* c, double* x, int32_t on_device) {
 to3d_status to3d_set_density(to3d_ctx* c, const double* x, int32_t on_device) {
     if (!c || !x) return TO3D_EINVAL;
     const size_t b = c->g.nel * sizeof(double);
+    if (!on_device)
+        for (long long e = 0; e < c->g.nel; ++e)
+            if (!(x[e] >= 0.0 && x[e] <= 1.0)) return set_err(c, TO3D_EINVAL, "densities must lie in [0, 1]");
     CK(cudaMemcpyAsync(c->x, x, b, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                        c->stream));
     if (!on_device) CK(cudaStreamSynchronize(c->stream));
+    return TO3D_OK;
+}
+
+to3d_status to3d_set_displacement(to3d_ctx* c, const double* u, int32_t on_device) {
+    if (!c || !u) return TO3D_EINVAL;
+    const size_t b = 3 * c->g.nnode * sizeof(double);
+    CK(cudaMemcpyAsync(c->u, u, b, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       c->stream));
+    if (!on_device) CK(cudaStreamSynchronize(c->stream));
+    c->have_u = true;
+    return TO3D_OK;
+}
+
+to3d_status to3d_get_iteration(const to3d_ctx* c, int32_t* iter) {
+    if (!c || !iter) return TO3D_EINVAL;
+    *iter = c->iter;
+    return TO3D_OK;
+}
+
+to3d_status to3d_set_iteration(to3d_ctx* c, int32_t iter) {
+    if (!c || iter < 0) return TO3D_EINVAL;
+    c->iter = iter;
     return TO3D_OK;
 }
 

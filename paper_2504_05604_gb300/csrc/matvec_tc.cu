@@ -851,3 +851,35 @@ void launch_soa_to_aos(to3d_ctx* c, cudaStream_t s, const float* q, const float*
 }
 
 }  // namespace to3d
+
+namespace to3d {
+
+// ------------------------------------------------------------------ wait self-test
+// One thread waits, with the tensor-core kernel's bounded suspend-and-poll
+// loop, on an mbarrier phase that nothing completes; it gives up after
+// `polls` polls and reports the timeout as the kernel would.
+__global__ void k_selftest_wait(int polls, int* status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+    const bool ok = tc::mbar_wait_sleep_bounded(&bar, 0u, (uint32_t)polls, 1000u);
+    *status = ok ? (int)TO3D_OK : (int)TO3D_ETIMEOUT;
+}
+
+}  // namespace to3d
+
+extern "C" TO3D_API to3d_status to3d_selftest_wait_timeout(int32_t polls, int32_t* status,
+                                                           void* stream) {
+    if (polls < 1 || polls > (1 << 16) || !status) return TO3D_EINVAL;
+    int* d = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMallocAsync((void**)&d, sizeof(int), s) != cudaSuccess) return TO3D_ENOMEM;
+    to3d::k_selftest_wait<<<1, 32, 0, s>>>(polls, d);
+    int h = -1;
+    cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TO3D_ECUDA;
+    *status = h;
+    return TO3D_OK;
+}

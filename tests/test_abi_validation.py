@@ -76,3 +76,22 @@ def test_entry_points_reject_null_context(lib):
     assert lib.to3d_launch_count(None) == 0
     lib.to3d_destroy(None)
     lib.to3d_batch_destroy(None)
+
+
+def test_create_rejects_non_finite_load(lib):
+    p = params(lib)
+    n = 3 * (p.nelx + 1) * (p.nely + 1) * (p.nelz + 1)
+    fx = np.zeros(n, np.uint8)
+    for bad in (np.nan, np.inf):
+        f = np.zeros(n)
+        f[5] = bad
+        h = C.c_void_p()
+        assert lib.to3d_create(C.byref(p), fx.ctypes.data, f.ctypes.data, None, None,
+                               C.byref(h)) == 1
+
+
+def test_selftest_rejects_bad_limits(lib):
+    st = C.c_int32()
+    assert lib.to3d_selftest_wait_timeout(0, C.byref(st), None) == 1
+    assert lib.to3d_selftest_wait_timeout(1 << 20, C.byref(st), None) == 1
+    assert lib.to3d_selftest_wait_timeout(8, None, None) == 1

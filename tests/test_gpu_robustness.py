@@ -1,0 +1,55 @@
+"""Failure detection and checkpoint/resume on the GPU, with no GPU fault:
+bounded waits report a timeout status, bad inputs are refused on the host,
+and a resumed context repeats the next OC iteration exactly."""
+import numpy as np
+import pytest
+
+from synth import problems
+from tests.gpu_helpers import lib_ctx
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def test_bounded_wait_times_out_and_the_context_stays_usable():
+    from paper_2504_05604_gb300 import BF16_DC
+    from paper_2504_05604_gb300.binding import STATUS, selftest_wait_timeout
+    st = selftest_wait_timeout(256)
+    assert st == 6, STATUS.get(st)          # TO3D_ETIMEOUT
+    prob = problems.cantilever(12, 6, 4)
+    rec = lib_ctx(prob, precision=BF16_DC).step()      # GPU still works afterwards
+    assert rec["status"] == 0 and rec["relres"] <= 1e-8
+
+
+def test_set_density_refuses_bad_values():
+    from paper_2504_05604_gb300 import To3dError
+    prob = problems.cantilever(6, 3, 2)
+    ctx = lib_ctx(prob)
+    for bad in (np.nan, -0.1, 1.5):
+        x = np.full(prob.nel, 0.3)
+        x[2] = bad
+        with pytest.raises(To3dError):
+            ctx.set_density(x)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_resume_repeats_the_next_iteration(tmp_path, precision):
+    prob = problems.cantilever(24, 8, 4, load="edge", volfrac=0.3, rmin=1.5)
+    a = lib_ctx(prob, precision=precision)
+    a.run(3)
+    path = str(tmp_path / "state.npz")
+    a.save_state(path)
+    nxt = a.step()
+    x_a = a.density()
+    b = lib_ctx(prob, precision=precision)
+    b.load_state(path)
+    assert b.iteration == 3
+    rb = b.step()
+    assert rb["compliance"] == nxt["compliance"]
+    assert rb["cg_iters"] == nxt["cg_iters"] and rb["halvings"] == nxt["halvings"]
+    assert np.array_equal(b.density(), x_a)
