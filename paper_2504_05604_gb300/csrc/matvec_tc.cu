@@ -305,13 +305,20 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
                 }
                 if (*vfail) break;
             }
+            if (*vfail) {
+                // after a timeout: let the copies already issued land before
+                // the CTA (and its shared memory) goes away; bounded as well
+                const uint32_t first = G > (uint32_t)NS ? G - (uint32_t)NS : 0u;
+                for (uint32_t k = first; k < G; ++k)
+                    tc::mbar_wait_sleep_bounded(&full[k % NS], (k / NS) & 1u, TC_WAIT_POLLS, 1000u);
+            }
         }
     } else if (warp == 9) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = tc::make_idesc_f16(128, NMMA, BF ? 1 : 0);
             const uint32_t a_addr = tc::smem_addr(sA), b_addr = tc::smem_addr(sB);
-            uint32_t H = 0;
+            uint32_t H = 0, issued = 0;
             for (int tile = blockIdx.x; tile < a.ntiles && !*vfail; tile += gridDim.x) {
                 int i0, j0, k0, nown;
                 tile_geom(tile, i0, j0, k0, nown);
@@ -332,7 +339,13 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
                         }
                     tc::mma_commit(&dfull[db]);
                     tc::mma_commit(&aempty[b]);
+                    issued = H + 1;
                 }
+            }
+            if (*vfail && issued) {
+                // after a timeout: the last MMAs must finish before TMEM is freed
+                const uint32_t h = issued - 1;
+                tc::mbar_wait_sleep_bounded(&aempty[h & 1], (h >> 1) & 1u, TC_WAIT_POLLS, 1000u);
             }
         }
     } else if (warp < 4) {
