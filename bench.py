@@ -30,6 +30,16 @@ if ROOT not in sys.path:
 METRIC = "OC iters/s at 480x160x80, chosen vs plain FP64 Jacobi-PCG at rel.res 1e-8"
 UNIT = "OC iters/s"
 PREC_NAMES = {0: "fp64", 1: "bf16-dc", 2: "bf16x2-dc", 3: "fp16-dc", 4: "fp16x2-dc"}
+# the arithmetic type of the tensor-core operand (the dominant kernel) and the
+# whole form in words
+DTYPES = {0: "f64", 1: "bf16", 2: "bf16", 3: "f16", 4: "f16"}
+ARITHMETIC = {
+    0: "f64 Jacobi-PCG, f64 matvec",
+    1: "bf16 operand x integer-exact bf16 stiffness, f32 accumulate, f32 inner CG, "
+       "f64 residual / dots / u (defect correction)",
+    2: "bf16 hi+lo operand, f32 accumulate, f32 inner CG, f64 defect correction",
+    3: "scaled f16 operand, f32 accumulate, f32 inner CG, f64 defect correction",
+    4: "scaled f16 hi+lo operand, f32 accumulate, f32 inner CG, f64 defect correction"}
 # FP64 Jacobi-PCG iterations per OC iteration, used to turn the oracle's
 # measured per-iteration cost into OC iterations/s when no GPU run in the
 # same process supplies the count (reference arm): the library's FP64 form
@@ -459,9 +469,10 @@ def ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16 operands, f32 inner CG, f64 defect correction" if args.precision else "f64",
+        "dtype": DTYPES[args.precision],
         "data": "synthetic",
-        "config": dict(workload_config(args, world), form=PREC_NAMES[args.precision]),
+        "config": dict(workload_config(args, world), form=PREC_NAMES[args.precision],
+                       arithmetic=ARITHMETIC[args.precision]),
         "gpu_launches": int(launches),
         "status": int(status),
         "cg_iters_per_step": its,
