@@ -315,8 +315,8 @@ typedef struct to3d_batch to3d_batch;
  * and bisection loops run on the device (conditional graph nodes); the
  * tensor-core kernel's z-segment length is autotuned per grid shape.  Only
  * the tensor-core defect-correction precisions are accepted (EINVAL for
- * TO3D_F64) with the sensitivity filter (EINVAL for TO3D_FILTER_DENS); the
- * device-side solver has no single- to two-slice escalation,
+ * TO3D_F64), with either filter; the device-side solver has no single- to
+ * two-slice escalation,
  * so the two-slice forms are the robust choice here (a single-slice solve
  * that stalls ends in TO3D_ENOCONV).  `stream`: the caller's stream that each step is ordered on. */
 TO3D_API to3d_status to3d_batch_create(int32_t nprob, const to3d_params* params,

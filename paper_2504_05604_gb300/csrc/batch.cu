@@ -213,9 +213,17 @@ static cudaError_t build_iter_graph(to3d_ctx* c) {
     DcCtl* ctl = (DcCtl*)c->dcctl;
     const int prec = c->prm.precision;
     const double target = c->prm.volfrac * (double)c->ndesign;
+    // density filter: analysis on xphys = H x / Hs (passive pinned), chain
+    // rule back to x; the OC update acts on x (as the single-context step)
+    const bool dens = c->prm.filter == TO3D_FILTER_DENS;
+    const double* xa = dens ? c->xphys : c->x;
     cudaGraph_t graph;
     CE(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
-    launch_simp(c, s0, c->x);
+    if (dens) {
+        launch_filter(c, s0, 1, c->x, nullptr, c->xphys);
+        launch_pin_passive(c, s0, c->xphys);
+    }
+    launch_simp(c, s0, xa);
     launch_diag(c, s0, c->E);
     launch_matvec64(c, s0, c->E, c->u, c->q, false);
     launch_residual64(c, s0, c->f, c->q, c->r, true);
@@ -237,8 +245,9 @@ static cudaError_t build_iter_graph(to3d_ctx* c) {
         k_dc_decide<<<1, 1, 0, s1>>>(ctl, c->ss, h_outer);
     }
     CE(end_while(s1));
-    launch_sensitivity(c, s0, c->x, c->u, c->ce, c->dc);
-    launch_filter(c, s0, 0, c->x, c->dc, c->dcf);
+    launch_sensitivity(c, s0, xa, c->u, c->ce, c->dc);
+    if (dens) launch_filter(c, s0, 2, c->dc, nullptr, c->dcf);
+    else launch_filter(c, s0, 0, c->x, c->dc, c->dcf);
     launch_oc_begin(c, s0, c->x, c->dcf, target);
     CE(new_handle(s0, &h_oc, 1));
     CE(begin_while(s0, s1, h_oc));
@@ -337,7 +346,6 @@ to3d_status to3d_batch_create(int32_t nprob, const to3d_params* params, const ui
     if (nprob < 1 || !params || !fixed || !load) return TO3D_EINVAL;
     for (int i = 0; i < nprob; ++i) {
         if (params[i].precision == TO3D_F64) return TO3D_EINVAL;   // tensor-core forms only
-        if (params[i].filter != TO3D_FILTER_SENS) return TO3D_EINVAL;   // sensitivity filter only
     }
     to3d_batch* b = new (std::nothrow) to3d_batch();
     if (!b) return TO3D_ENOMEM;
@@ -375,6 +383,8 @@ to3d_status to3d_batch_create(int32_t nprob, const to3d_params* params, const ui
             cudaMalloc(&c->dcctl, sizeof(DcCtl)) != cudaSuccess ||
             cudaMallocHost(&c->dcctl_h, sizeof(DcCtl)) != cudaSuccess ||
             cudaMemcpy(c->dcctl, &h, sizeof(DcCtl), cudaMemcpyHostToDevice) != cudaSuccess ||
+            (c->prm.filter == TO3D_FILTER_DENS &&
+             cudaMalloc(&c->xphys, sizeof(double) * c->g.nel) != cudaSuccess) ||
             autotune_tc(c) != cudaSuccess || build_iter_graph(c) != cudaSuccess) {
             batch_free(b);
             return TO3D_ECUDA;

@@ -75,3 +75,20 @@ def test_full_synthetic_batch_properties():
         if prob.passive is not None:
             assert np.all(x[prob.passive == 1] == 0.0)
     batch.close()
+
+
+def test_batch_density_filter_matches_oracle_loop():
+    from paper_2504_05604_gb300 import FILTER_DENS, Batch
+    probs = small_batch()[:2]
+    iters = 3
+    batch = Batch(probs, precision=2, filter=FILTER_DENS)
+    recs = [batch.step() for _ in range(iters)]
+    for i, prob in enumerate(probs):
+        x_ref, hist = topopt.top3d(prob, iters=iters, solver="direct", filter_kind="density")
+        for it in range(iters):
+            r, h = recs[it][i], hist[it]
+            assert r["status"] == 0 and r["relres"] <= 1e-8
+            assert r["compliance"] == pytest.approx(h.compliance, rel=1e-5)
+            assert r["halvings"] == h.halvings
+        assert np.abs(batch.density(i) - x_ref).max() <= 1e-4
+    batch.close()
