@@ -221,8 +221,9 @@ TO3D_API to3d_status to3d_oc_update(to3d_ctx* ctx, const double* x, const double
                            int32_t on_device);
 
 /* ---- learned preconditioner ----------------------------------------------
- * Not in the paper, whose solver is plain PCG (Section 2.3, Table 2): an
- * optional preconditioner for the same FP64 state equation.
+ * Not in the paper, which solves K U = F with a sparse direct solver
+ * (Section 2.2): an optional preconditioner for the library's iterative
+ * solve of the same FP64 state equation.
  * A four-level U-Net on the node grid (16/32/64/64 channels, 3x3x3
  * convolutions with zero padding, 2x2x2 average pooling, nearest x2
  * upsampling with skip concatenation, ReLU), applied as z = M(r) inside
@@ -356,7 +357,10 @@ TO3D_API to3d_status to3d_selftest_wait_timeout(int32_t polls, int32_t* status, 
  * (32768 blocks of 256); larger grids return TO3D_EINVAL, as do non-positive
  * sizes, null pointers and out-of-range parameters.  The first call on each
  * device looks up the array's device address; make that first call before
- * any stream capture.  All calls share the array, and each call leaves its
+ * any stream capture.  That address belongs to the device's primary
+ * context: after cudaDeviceReset (or any other release and re-creation of
+ * that context) in the same process it is stale, so do not call this entry
+ * point again in a process that has reset the device.  All calls share the array, and each call leaves its
  * contents behind (the call clears what must start at zero), so calls that
  * overlap on the GPU -- on different streams or from different threads --
  * race on it and must be serialised by the caller.

@@ -13,6 +13,8 @@ classic sensitivity filter that the SIMP/OC literature pairs with OC):
     dc~_e = sum_i H_ei x_i dc_i / (Hs_e max(1e-3, x_e))
 
 Density filter: x~ = H x / Hs, with chain rule dc_e = sum_i H_ie dc_i / Hs_i.
+Where passive elements i are pinned after filtering (x~_i = 0 or 1), x~_i
+does not depend on x, so their terms drop out of the chain rule.
 """
 from __future__ import annotations
 
@@ -77,8 +79,14 @@ def density_filter(H, Hs, x) -> np.ndarray:
     return (H @ x) / Hs
 
 
-def density_filter_chain(H, Hs, dc) -> np.ndarray:
-    return H.T @ (dc / Hs)
+def density_filter_chain(H, Hs, dc, passive=None) -> np.ndarray:
+    """d/dx of a function of the filtered field, given its gradient dc with
+    respect to the filtered field.  Elements whose filtered value is pinned
+    (passive != 0) contribute nothing."""
+    g = dc / Hs
+    if passive is not None:
+        g = np.where(np.asarray(passive) != 0, 0.0, g)
+    return H.T @ g
 
 
 def _shift_sum(nelx, nely, nelz, rmin, v):

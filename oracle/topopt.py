@@ -52,6 +52,33 @@ def analyse(prob, x, KE, f, solver="direct", rtol=1e-12, x0=None):
     return u, ce, c, dc, its
 
 
+def physical_density(prob, x, H, Hs, filter_kind):
+    """The field the analysis sees: x itself (sensitivity filter), or the
+    filtered field H x / Hs with passive elements pinned (density filter,
+    Section 2.4 with the passive regions of Section 2.3)."""
+    if filter_kind != "density":
+        return x
+    passive = prob.passive_or_zeros()
+    xphys = filters.density_filter(H, Hs, x)
+    xphys[passive == 1] = 0.0
+    xphys[passive == 2] = 1.0
+    return xphys
+
+
+def filtered_sensitivity(prob, x, xphys, H, Hs, KE, f, filter_kind, solver="direct",
+                         rtol=1e-12, x0=None):
+    """Analysis on xphys and the sensitivities the OC update receives:
+    returns (u, c, dcf, pcg_iters).  Sensitivity filter: dcf = H(x dc) /
+    (Hs max(1e-3, x)).  Density filter: dcf = d c(xphys(x)) / dx by the chain
+    rule through the filter; pinned elements carry nothing back."""
+    u, ce, c, dc, its = analyse(prob, xphys, KE, f, solver=solver, rtol=rtol, x0=x0)
+    if filter_kind == "density":
+        dcf = filters.density_filter_chain(H, Hs, dc, prob.passive_or_zeros())
+    else:
+        dcf = filters.sensitivity_filter(H, Hs, x, dc)
+    return u, c, dcf, its
+
+
 def top3d(prob, iters=None, solver="direct", rtol=1e-12, filter_kind="sensitivity",
           x_init=None):
     """Run the loop; returns (x, history list of IterRecord)."""
@@ -64,17 +91,10 @@ def top3d(prob, iters=None, solver="direct", rtol=1e-12, filter_kind="sensitivit
     hist: List[IterRecord] = []
     u = None
     for it in range(iters):
-        if filter_kind == "density":
-            xphys = filters.density_filter(H, Hs, x)
-            xphys[passive == 1] = 0.0
-            xphys[passive == 2] = 1.0
-        else:
-            xphys = x
-        u, ce, c, dc, its = analyse(prob, xphys, KE, f, solver=solver, rtol=rtol, x0=u)
-        if filter_kind == "density":
-            dcf = filters.density_filter_chain(H, Hs, dc)
-        else:
-            dcf = filters.sensitivity_filter(H, Hs, x, dc)
+        # the OC update and its volume act on x (also with the density filter)
+        xphys = physical_density(prob, x, H, Hs, filter_kind)
+        u, c, dcf, its = filtered_sensitivity(prob, x, xphys, H, Hs, KE, f, filter_kind,
+                                              solver=solver, rtol=rtol, x0=u)
         xnew, lam, nh, vol = oc.oc_update(x, dcf, prob.volfrac, passive, prob.move,
                                           prob.bisect_tol)
         ndes = max(1, int(np.count_nonzero(passive == 0)))

@@ -160,6 +160,15 @@ class _Arg:
             self.obj, self.ptr, self.dev = arr, arr.ctypes.data, 0
 
 
+def _need(arg, n, name):
+    """Refuse an array shorter or longer than the grid implies before its
+    pointer reaches the library (which reads and writes exactly n entries)."""
+    got = int(arg.obj.numel()) if _is_torch(arg.obj) else int(arg.obj.size)
+    if got != n:
+        raise ValueError(f"{name} has {got} entries, the grid needs {n}")
+    return arg
+
+
 def _same_kind(*args):
     devs = {a.dev for a in args if a is not None}
     if len(devs) > 1:
@@ -247,16 +256,16 @@ class Context:
 
     def density(self, out=None):
         out = np.empty(self.nel) if out is None else out
-        a = _Arg(out, np.float64)
+        a = _need(_Arg(out, np.float64), self.nel, "x")
         self._check(self.lib.to3d_get_density(self.h, a.ptr, a.dev), "get_density")
         return out
 
     def set_density(self, x):
-        a = _Arg(x, np.float64)
+        a = _need(_Arg(x, np.float64), self.nel, "x")
         self._check(self.lib.to3d_set_density(self.h, a.ptr, a.dev), "set_density")
 
     def set_displacement(self, u):
-        a = _Arg(u, np.float64)
+        a = _need(_Arg(u, np.float64), self.ndof, "u")
         self._check(self.lib.to3d_set_displacement(self.h, a.ptr, a.dev), "set_displacement")
 
     @property
@@ -279,21 +288,25 @@ class Context:
 
     def displacement(self, out=None):
         out = np.empty(self.ndof) if out is None else out
-        a = _Arg(out, np.float64)
+        a = _need(_Arg(out, np.float64), self.ndof, "u")
         self._check(self.lib.to3d_get_displacement(self.h, a.ptr, a.dev), "get_displacement")
         return out
 
     # ---- single steps
     def matvec(self, x, p, y=None):
         y = np.empty(self.ndof) if y is None else y
-        ax, ap, ay = _Arg(x, np.float64), _Arg(p, np.float64), _Arg(y, np.float64)
+        ax, ap, ay = (_need(_Arg(x, np.float64), self.nel, "x"),
+                      _need(_Arg(p, np.float64), self.ndof, "p"),
+                      _need(_Arg(y, np.float64), self.ndof, "y"))
         dev = _same_kind(ax, ap, ay)
         self._check(self.lib.to3d_matvec(self.h, ax.ptr, ap.ptr, ay.ptr, dev), "matvec")
         return y
 
     def matvec_lowp(self, x, p32, prec=BF16_DC, y=None):
         y = np.empty(self.ndof, np.float32) if y is None else y
-        ax, ap, ay = _Arg(x, np.float64), _Arg(p32, np.float32), _Arg(y, np.float32)
+        ax, ap, ay = (_need(_Arg(x, np.float64), self.nel, "x"),
+                      _need(_Arg(p32, np.float32), self.ndof, "p"),
+                      _need(_Arg(y, np.float32), self.ndof, "y"))
         dev = _same_kind(ax, ap, ay)
         self._check(self.lib.to3d_matvec_lowp(self.h, ax.ptr, ap.ptr, ay.ptr, prec, dev),
                     "matvec_lowp")
@@ -301,8 +314,8 @@ class Context:
 
     def solve(self, x, f=None, u=None):
         u = np.zeros(self.ndof) if u is None else u
-        ax, au = _Arg(x, np.float64), _Arg(u, np.float64)
-        af = _Arg(f, np.float64) if f is not None else None
+        ax, au = _need(_Arg(x, np.float64), self.nel, "x"), _need(_Arg(u, np.float64), self.ndof, "u")
+        af = _need(_Arg(f, np.float64), self.ndof, "f") if f is not None else None
         dev = _same_kind(ax, au, af)
         info = SolveInfo()
         st = self.lib.to3d_solve(self.h, ax.ptr, af.ptr if af else None, au.ptr, dev,
@@ -314,8 +327,10 @@ class Context:
     def sensitivity(self, x, u, ce=None, dc=None):
         ce = np.empty(self.nel) if ce is None else ce
         dc = np.empty(self.nel) if dc is None else dc
-        ax, au, ac, ad = (_Arg(x, np.float64), _Arg(u, np.float64), _Arg(ce, np.float64),
-                          _Arg(dc, np.float64))
+        ax, au, ac, ad = (_need(_Arg(x, np.float64), self.nel, "x"),
+                          _need(_Arg(u, np.float64), self.ndof, "u"),
+                          _need(_Arg(ce, np.float64), self.nel, "ce"),
+                          _need(_Arg(dc, np.float64), self.nel, "dc"))
         dev = _same_kind(ax, au, ac, ad)
         comp = C.c_double()
         self._check(self.lib.to3d_sensitivity(self.h, ax.ptr, au.ptr, ac.ptr, ad.ptr,
@@ -324,8 +339,8 @@ class Context:
 
     def filter(self, v, x=None, kind=FILTER_SENS, transpose=False, out=None):
         out = np.empty(self.nel) if out is None else out
-        av, ao = _Arg(v, np.float64), _Arg(out, np.float64)
-        ax = _Arg(x, np.float64) if x is not None else None
+        av, ao = _need(_Arg(v, np.float64), self.nel, "v"), _need(_Arg(out, np.float64), self.nel, "out")
+        ax = _need(_Arg(x, np.float64), self.nel, "x") if x is not None else None
         dev = _same_kind(av, ao, ax)
         self._check(self.lib.to3d_filter_apply(self.h, kind, ax.ptr if ax else None, av.ptr,
                                                ao.ptr, int(transpose), dev), "filter")
@@ -333,7 +348,9 @@ class Context:
 
     def oc_update(self, x, dcf, xnew=None):
         xnew = np.empty(self.nel) if xnew is None else xnew
-        ax, ad, an = _Arg(x, np.float64), _Arg(dcf, np.float64), _Arg(xnew, np.float64)
+        ax, ad, an = (_need(_Arg(x, np.float64), self.nel, "x"),
+                      _need(_Arg(dcf, np.float64), self.nel, "dcf"),
+                      _need(_Arg(xnew, np.float64), self.nel, "xnew"))
         dev = _same_kind(ax, ad, an)
         lam, vol, nh = C.c_double(), C.c_double(), I32()
         self._check(self.lib.to3d_oc_update(self.h, ax.ptr, ad.ptr, an.ptr, C.byref(lam),
@@ -360,14 +377,18 @@ class Context:
 
     def cnn_apply(self, x, r, z=None):
         z = np.empty(self.ndof) if z is None else z
-        ax, ar, az = _Arg(x, np.float64), _Arg(r, np.float64), _Arg(z, np.float64)
+        ax, ar, az = (_need(_Arg(x, np.float64), self.nel, "x"),
+                      _need(_Arg(r, np.float64), self.ndof, "r"),
+                      _need(_Arg(z, np.float64), self.ndof, "z"))
         dev = _same_kind(ax, ar, az)
         self._check(self.lib.to3d_cnn_apply(self.h, ax.ptr, ar.ptr, az.ptr, dev), "cnn_apply")
         return z
 
     def cnn_loss_grad(self, x, r, e):
         g = np.empty(self.cnn_param_count(), np.float32)
-        ax, ar, ae = _Arg(x, np.float64), _Arg(r, np.float64), _Arg(e, np.float64)
+        ax, ar, ae = (_need(_Arg(x, np.float64), self.nel, "x"),
+                      _need(_Arg(r, np.float64), self.ndof, "r"),
+                      _need(_Arg(e, np.float64), self.ndof, "e"))
         dev = _same_kind(ax, ar, ae)
         loss = C.c_double()
         self._check(self.lib.to3d_cnn_loss_grad(self.h, ax.ptr, ar.ptr, ae.ptr, dev,
@@ -450,7 +471,10 @@ def sensitivity_noalloc(nelx, nely, nelz, x, u, ce, dc, penal=3.0, E0=1.0, Emin=
     with no device allocation by the library (``to3d_sensitivity_noalloc``).
     x, u are inputs and ce, dc outputs: contiguous CUDA float64 tensors.
     Returns the compliance."""
-    args = [_Arg(t, np.float64) for t in (x, u, ce, dc)]
+    nel = int(nelx) * int(nely) * int(nelz)
+    ndof = 3 * (int(nelx) + 1) * (int(nely) + 1) * (int(nelz) + 1)
+    args = [_need(_Arg(t, np.float64), n, name)
+            for t, n, name in ((x, nel, "x"), (u, ndof, "u"), (ce, nel, "ce"), (dc, nel, "dc"))]
     if any(a.dev != 1 for a in args):
         raise TypeError("sensitivity_noalloc takes CUDA tensors only")
     if stream is None:

@@ -909,7 +909,8 @@ to3d_status to3d_step(to3d_ctx* c, to3d_iter_info* info) {
     to3d_status st;
     // density filter (Section 2.4): the analysis runs on the filtered field
     // xphys = H x / Hs (passive elements pinned), and the chain rule carries
-    // its sensitivities back, dc_x = H^T (dc / Hs); the OC update acts on x
+    // its sensitivities back, dc_x = H^T (dc / Hs) over the unpinned
+    // elements; the OC update and its volume act on x
     const bool dens = c->prm.filter == TO3D_FILTER_DENS;
     if (dens && !c->xphys && cudaMalloc(&c->xphys, sizeof(double) * c->g.nel) != cudaSuccess)
         return set_err(c, TO3D_ENOMEM, "filtered densities");
@@ -927,8 +928,12 @@ to3d_status to3d_step(to3d_ctx* c, to3d_iter_info* info) {
     launch_sensitivity(c, s, xa, c->u, c->ce, c->dc);
     LK("sensitivity");
     CK(cudaEventRecord(c->ev[2], s));
-    if (dens) launch_filter(c, s, 2, c->dc, nullptr, c->dcf);
-    else launch_filter(c, s, 0, c->x, c->dc, c->dcf);
+    if (dens) {
+        launch_zero_passive(c, s, c->dc);
+        launch_filter(c, s, 2, c->dc, nullptr, c->dcf);
+    } else {
+        launch_filter(c, s, 0, c->x, c->dc, c->dcf);
+    }
     LK("filter");
     CK(cudaEventRecord(c->ev[3], s));
     const double target = c->prm.volfrac * (double)c->ndesign;

@@ -214,7 +214,8 @@ static cudaError_t build_iter_graph(to3d_ctx* c) {
     const int prec = c->prm.precision;
     const double target = c->prm.volfrac * (double)c->ndesign;
     // density filter: analysis on xphys = H x / Hs (passive pinned), chain
-    // rule back to x; the OC update acts on x (as the single-context step)
+    // rule back to x over the unpinned elements; the OC update acts on x (as
+    // the single-context step)
     const bool dens = c->prm.filter == TO3D_FILTER_DENS;
     const double* xa = dens ? c->xphys : c->x;
     cudaGraph_t graph;
@@ -246,8 +247,12 @@ static cudaError_t build_iter_graph(to3d_ctx* c) {
     }
     CE(end_while(s1));
     launch_sensitivity(c, s0, xa, c->u, c->ce, c->dc);
-    if (dens) launch_filter(c, s0, 2, c->dc, nullptr, c->dcf);
-    else launch_filter(c, s0, 0, c->x, c->dc, c->dcf);
+    if (dens) {
+        launch_zero_passive(c, s0, c->dc);
+        launch_filter(c, s0, 2, c->dc, nullptr, c->dcf);
+    } else {
+        launch_filter(c, s0, 0, c->x, c->dc, c->dcf);
+    }
     launch_oc_begin(c, s0, c->x, c->dcf, target);
     CE(new_handle(s0, &h_oc, 1));
     CE(begin_while(s0, s1, h_oc));

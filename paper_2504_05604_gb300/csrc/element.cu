@@ -267,18 +267,28 @@ void launch_sensitivity_raw(const KE64& ke, const Grid& g, cudaStream_t s, const
 }
 
 // passive elements keep their pinned density: void 0, solid 1
+// v_e = void_val on void and solid_val on solid passive elements
 __global__ void k_pin_passive(long long nel, const uint8_t* __restrict__ passive,
-                              double* __restrict__ x) {
+                              double* __restrict__ x, double void_val, double solid_val) {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= nel) return;
     const uint8_t t = passive[e];
-    if (t == 1) x[e] = 0.0;
-    else if (t == 2) x[e] = 1.0;
+    if (t == 1) x[e] = void_val;
+    else if (t == 2) x[e] = solid_val;
 }
 
 void launch_pin_passive(to3d_ctx* c, cudaStream_t s, double* x) {
     if (!c->passive) return;
-    k_pin_passive<<<el_blocks(c->g.nel), EL_THREADS, 0, s>>>(c->g.nel, c->passive, x);
+    k_pin_passive<<<el_blocks(c->g.nel), EL_THREADS, 0, s>>>(c->g.nel, c->passive, x, 0.0, 1.0);
+    c->launches++;
+}
+
+// The filtered densities of passive elements are pinned, so they do not
+// depend on x: their sensitivities carry nothing back through the density
+// filter's chain rule.
+void launch_zero_passive(to3d_ctx* c, cudaStream_t s, double* v) {
+    if (!c->passive) return;
+    k_pin_passive<<<el_blocks(c->g.nel), EL_THREADS, 0, s>>>(c->g.nel, c->passive, v, 0.0, 0.0);
     c->launches++;
 }
 

@@ -198,6 +198,7 @@ bool prepare_tc_operands(to3d_ctx* c);
 
 // element.cu
 void launch_pin_passive(to3d_ctx* c, cudaStream_t s, double* x);
+void launch_zero_passive(to3d_ctx* c, cudaStream_t s, double* v);
 void launch_sensitivity(to3d_ctx* c, cudaStream_t s, const double* x, const double* u,
                         double* ce, double* dc);
 void launch_hs(to3d_ctx* c, cudaStream_t s);

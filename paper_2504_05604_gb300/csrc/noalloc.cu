@@ -27,7 +27,9 @@ constexpr size_t kNoAllocScratchBytes = kNoAllocPartialBytes + 256;   // + count
 // 256 KiB + 256 B, held by every GPU that loads the library until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of the scratch array, looked up once per device.  In host
+// Device address of the scratch array, looked up once per device (it stays
+// valid while the device's primary context lives; a device reset in the same
+// process makes it stale, which the header documents).  In host
 // code the symbol g_noalloc_scratch is only a host-side stand-in: handing it
 // to a kernel would fault (or, where the GPU can reach host memory, silently
 // use the wrong memory), so the real address comes from

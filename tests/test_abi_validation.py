@@ -95,3 +95,29 @@ def test_selftest_rejects_bad_limits(lib):
     assert lib.to3d_selftest_wait_timeout(0, C.byref(st), None) == 1
     assert lib.to3d_selftest_wait_timeout(1 << 20, C.byref(st), None) == 1
     assert lib.to3d_selftest_wait_timeout(8, None, None) == 1
+
+
+def test_noalloc_rejects_too_large_grid_before_any_cuda_call(lib):
+    """The allocation-free entry point checks the grid against its fixed
+    scratch before touching the GPU: non-null dummy pointers are never used."""
+    d = np.zeros(4)
+    comp = C.c_double()
+    p = d.ctypes.data
+    assert lib.to3d_sensitivity_noalloc(2049, 2048, 2, 3.0, 1.0, 1e-9, 0.3, p, p, p, p,
+                                        C.byref(comp), None) == 1
+    assert lib.to3d_sensitivity_noalloc(0, 4, 4, 3.0, 1.0, 1e-9, 0.3, p, p, p, p,
+                                        C.byref(comp), None) == 1
+    assert lib.to3d_sensitivity_noalloc(4, 4, 4, 3.0, 1.0, 1e-9, 0.5, p, p, p, p,
+                                        C.byref(comp), None) == 1
+
+
+def test_binding_refuses_arrays_of_the_wrong_length(lib):
+    from paper_2504_05604_gb300 import binding
+    ok, short = np.zeros(4 * 3 * 2), np.zeros(5)
+    u = np.zeros(3 * 5 * 4 * 3)
+    with pytest.raises(ValueError):
+        binding.sensitivity_noalloc(4, 3, 2, short, u, ok, ok)
+    with pytest.raises(ValueError):
+        binding.sensitivity_noalloc(4, 3, 2, ok, short, ok, ok)
+    with pytest.raises(ValueError):
+        binding.sensitivity_noalloc(4, 3, 2, ok, u, ok, short)

@@ -2,7 +2,8 @@
 
 CPU: the oracle reproduces the stored values (regression pin of the stored
 file against its generator) and the stored volumes are on target to 1e-6.
-GPU: the library's loop, FP64 and BF16 hi+lo forms, against the stored
+GPU: the library's loop, FP64 and the tensor-core forms (single-slice BF16,
+the benchmark's form; BF16 hi+lo; scaled FP16), against the stored
 trajectory: first ten compliances to 1e-5, final compliance to 1e-3 (the
 final-design bar), volume on target to 1e-6 in every iteration.
 """
@@ -46,7 +47,7 @@ def test_stored_volumes_on_target():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", [0, 2])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
 def test_gpu_loop_matches_stored_trajectory(precision):
     import __graft_entry__ as ge
     ge.build()

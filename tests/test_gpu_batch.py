@@ -80,6 +80,11 @@ def test_full_synthetic_batch_properties():
 def test_batch_density_filter_matches_oracle_loop():
     from paper_2504_05604_gb300 import FILTER_DENS, Batch
     probs = small_batch()[:2]
+    # a solid passive slab under the load of the first problem
+    pas = np.zeros(probs[0].nel, np.uint8)
+    k, j, i = np.meshgrid(np.arange(4), np.arange(8), np.arange(20), indexing="ij")
+    pas[((i >= 17) & (j == 0)).ravel()] = 2
+    probs[0].passive = pas
     iters = 3
     batch = Batch(probs, precision=2, filter=FILTER_DENS)
     recs = [batch.step() for _ in range(iters)]

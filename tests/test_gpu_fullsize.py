@@ -61,7 +61,7 @@ def test_full_size_matvecs_on_sampled_rows(big):
 
 def test_full_size_oc_iteration_properties(big):
     """One OC iteration of the benchmark's form from x0: true FP64 residual at
-    most 1e-8, volume on target to the bisection tolerance, the energy
+    most 1e-8 (the library's own and the oracle's recomputation), volume on target to the bisection tolerance, the energy
     identity f^T u = sum E_e ce_e, and ce_e = u_e^T KE u_e on sampled
     elements of the library's own displacement."""
     from paper_2504_05604_gb300 import BF16_DC
@@ -74,10 +74,17 @@ def test_full_size_oc_iteration_properties(big):
     f = fem.masked_load(prob.load, prob.fixed)
     x0 = prob.initial_density()
     fu = float(f @ u)
+    # the true residual recomputed with the oracle's operator (element sum,
+    # FP64): the two evaluations of f - K u differ only by rounding
+    KE = fem.element_stiffness(prob.nu)
+    E0 = fem.simp_modulus(x0, prob.penal, prob.E0, prob.Emin)
+    Ku = fem.matvec_elementwise(prob.nelx, prob.nely, prob.nelz, E0, KE, u, prob.fixed)
+    relres = np.linalg.norm(f - Ku) / np.linalg.norm(f)
+    assert relres <= 1.01e-8, relres
+    del Ku
     ce, dc, c = ctx.sensitivity(x0, u)
     assert c == pytest.approx(fu, rel=1e-6)
     assert rec["compliance"] == pytest.approx(c, rel=1e-12)
-    KE = fem.element_stiffness(prob.nu)
     rng = np.random.Generator(np.random.PCG64(64))
     els = np.concatenate([rng.choice(prob.nel, 200, replace=False), [0, prob.nel - 1]])
     nx, ny = prob.nelx + 1, prob.nely + 1

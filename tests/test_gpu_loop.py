@@ -15,7 +15,7 @@ def _built():
     g.build()
 
 
-@pytest.mark.parametrize("precision", [0, 2])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
 def test_trajectory_matches_oracle(precision):
     prob = problems.cantilever(30, 10, 4, load="edge", volfrac=0.3, rmin=1.5)
     iters = 12
@@ -41,7 +41,7 @@ def test_passive_void_cylinder_step():
     for r, h in zip(recs, hist):
         assert r["compliance"] == pytest.approx(h.compliance, rel=1e-5)
     x = ctx.density()
-    assert np.all(x[pas == 1] == 0.0)
+    assert np.all(x[pas == 1] == 0.0) and np.all(x[pas == 2] == 1.0)
     assert np.abs(x - x_ref).max() <= 1e-4
 
 
@@ -53,10 +53,15 @@ def test_smoke_entry():
 @pytest.mark.parametrize("precision", [0, 1])
 def test_density_filter_trajectory_matches_oracle(precision):
     """Density-filter OC (Section 2.4): analysis on H x / Hs, chain rule
-    H^T (dc / Hs), OC on x; with a passive void region."""
+    H^T (dc / Hs) over the unpinned elements, OC on x; with passive void and
+    solid regions."""
     from paper_2504_05604_gb300 import FILTER_DENS
     nelx, nely, nelz = 30, 10, 4
     pas = problems.void_cylinder_z(nelx, nely, nelz, 15.0, 5.0, 2.5)
+    # a solid passive block under the loaded edge: its pinned filtered
+    # densities carry no sensitivity back through the filter
+    k, j, i = np.meshgrid(np.arange(nelz), np.arange(nely), np.arange(nelx), indexing="ij")
+    pas[((i >= nelx - 3) & (j <= 1)).ravel()] = 2
     prob = problems.cantilever(nelx, nely, nelz, load="edge", volfrac=0.3, rmin=1.5,
                                passive=pas)
     iters = 8
@@ -68,5 +73,5 @@ def test_density_filter_trajectory_matches_oracle(precision):
         assert r["compliance"] == pytest.approx(h.compliance, rel=1e-5)
         assert r["halvings"] == h.halvings
     x = ctx.density()
-    assert np.all(x[pas == 1] == 0.0)
+    assert np.all(x[pas == 1] == 0.0) and np.all(x[pas == 2] == 1.0)
     assert np.abs(x - x_ref).max() <= 1e-4

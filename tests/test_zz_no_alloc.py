@@ -46,10 +46,18 @@ def test_noalloc_matches_context_entry_point_twice():
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch():
+    """A grid one row past the scratch limit, with buffers of the full size
+    that grid needs (so nothing could be read or written out of bounds even
+    if the limit check were absent): refused with TO3D_EINVAL."""
     import torch
     from paper_2504_05604_gb300 import binding
 
-    t = torch.zeros(4, dtype=torch.float64, device="cuda")
+    nelx, nely, nelz = 2049, 2048, 2                          # 8,392,704 > 8,388,608 elements
+    nel = nelx * nely * nelz
+    ndof = 3 * (nelx + 1) * (nely + 1) * (nelz + 1)
+    x = torch.zeros(nel, dtype=torch.float64, device="cuda")
+    u = torch.zeros(ndof, dtype=torch.float64, device="cuda")
+    ce, dc = torch.empty_like(x), torch.empty_like(x)
     with pytest.raises(binding.To3dError) as ei:
-        binding.sensitivity_noalloc(2049, 2048, 2, t, t, t, t)   # 8,392,704 > 8,388,608 elements
+        binding.sensitivity_noalloc(nelx, nely, nelz, x, u, ce, dc)
     assert ei.value.status == 1
