@@ -16,10 +16,12 @@ Each function is a plain, slow, checkable restatement of what the paper
                  Lagrange multiplier and move limits (Section 2.3).
 * ``topopt``  -- the optimisation loop (Section 2.5).
 * ``cnn``     -- naive FP64 3D convolutions, forward and backward, for the
-                 learned preconditioner.
+                 learned U-Net preconditioner.
+* ``mg``      -- the learned multigrid preconditioner: hierarchy, coarse
+                 moduli, transfer operators, V-cycle and its training loss.
 
 Parity status of each function is stated in its docstring; all functions
 here are pinned by ``tests/test_oracle_*.py`` against closed forms,
 invariants or brute force.
 """
-from . import fem, filters, oc, topopt  # noqa: F401
+from . import fem, filters, mg, oc, topopt  # noqa: F401
