@@ -71,7 +71,11 @@ typedef enum {
     TO3D_FP16X2_DC = 4   /* scaled FP16 hi + lo slices (about 22 bits)        */
 } to3d_precision;
 
-typedef enum { TO3D_JACOBI = 0, TO3D_CNN_FCG = 1 } to3d_precond;
+/* Preconditioner of the equilibrium solve (none is in the paper, which uses
+ * a sparse direct solver, Section 2.2).  TO3D_LMG: the learned multigrid
+ * V-cycle (to3d_mg_*); with TO3D_F64 it preconditions FP64 flexible CG,
+ * with a *_DC precision the FP32 inner CG of the defect correction. */
+typedef enum { TO3D_JACOBI = 0, TO3D_CNN_FCG = 1, TO3D_LMG = 2 } to3d_precond;
 typedef enum { TO3D_FILTER_SENS = 0, TO3D_FILTER_DENS = 1 } to3d_filter;
 
 typedef struct {
@@ -96,7 +100,9 @@ typedef struct {
                             * that flexible CG must keep pace with before the
                             * context has timed a plain solve of its own (0:
                             * no such bound until then)                       */
-    int32_t reserved[5];
+    int32_t mg_sweeps;   /* TO3D_LMG: Jacobi sweeps on the coarsest level
+                          * (0: 16)                                           */
+    int32_t reserved[4];
 } to3d_params;
 
 typedef struct {
@@ -307,6 +313,53 @@ TO3D_API to3d_status to3d_conv3d_backward(int32_t Z, int32_t Y, int32_t X, int32
                                           float* gx, float* gw, float* gb, void* stream);
 
 /* ---- many independent problems ------------------------------------------ */
+
+/* ---- learned multigrid preconditioner (params.precond = TO3D_LMG) ----------
+ * Not in the paper, which solves K U = F with a sparse direct solver
+ * (Section 2.2): a preconditioner for the library's iterative solve of the
+ * same state equation, K = sum_e E_e KE with E_e from the SIMP law of
+ * Section 2.3.  A geometric multigrid V-cycle:
+ *   levels     element counts halved (rounded up) until the largest is at
+ *              most 4 or the smallest below 2; coarse node C on fine node
+ *              2C; a coarse dof is clamped when the fine dof at 2C is;
+ *   coarse K   coarse element modulus s_l (mean over its 8 child slots of
+ *              E^q_l)^(1/q_l), children past the grid counted as 0, times
+ *              the unit KE (s = 2 gives the Galerkin operator for a uniform
+ *              modulus);
+ *   transfer   trilinear prolongation P, restriction P^T, clamped dofs 0;
+ *   smoother   damped Jacobi with weight w_l, one sweep before and one after
+ *              the coarse correction; params.mg_sweeps sweeps (default 16)
+ *              on the coarsest level.
+ * The cycle runs in FP32 with the tensor-core operator (the context's
+ * operand form; BF16 for TO3D_F64) on every level.  With TO3D_F64 it
+ * preconditions FP64 flexible CG (the Jacobi-PCG fallback as for
+ * TO3D_CNN_FCG); with a *_DC precision it preconditions the FP32 inner CG,
+ * which restarts at each FP64 residual replacement (every drop by
+ * params.inner_rtol).
+ * Parameters theta (10 doubles, to3d_mg_param_count): w_0, w_1, w_2, w_3,
+ * q_1, q_2, q_3, s_1, s_2, s_3, where index g applies to level min(l, 3), so
+ * parameters learned on one grid size apply to any other.  Defaults: w = 0.5,
+ * q = 1, s = 2.  Valid ranges: 0 < w < 1, 1/8 <= q <= 8, 0 < s <= 64
+ * (TO3D_EINVAL otherwise).  The first call that needs the hierarchy creates
+ * one coarse context per level (device allocations). */
+TO3D_API to3d_status to3d_mg_param_count(to3d_ctx* ctx, int64_t* n);
+TO3D_API to3d_status to3d_mg_get_params(to3d_ctx* ctx, double* theta, int64_t n);
+TO3D_API to3d_status to3d_mg_set_params(to3d_ctx* ctx, const double* theta, int64_t n);
+/* Number of levels of the hierarchy (1 = the design grid only). */
+TO3D_API to3d_status to3d_mg_levels(to3d_ctx* ctx, int32_t* nlev);
+/* z = V r for densities x [nel] and a residual r [3N] (FP64, clamped
+ * entries ignored; z is 0 there), host or device as `on_device` says. */
+TO3D_API to3d_status to3d_mg_apply(to3d_ctx* ctx, const double* x, const double* r, double* z,
+                                   int32_t on_device);
+/* Learn theta on the context's current design: `nsnap` residuals of FP64
+ * Jacobi-PCG from u = 0 after a random number (0..200) of iterations (seed
+ * `seed`), each with r^T K^-1 r from an FP64 solve to 1e-10; then `steps`
+ * Adam steps (rate lr) on central-difference gradients of the mean
+ * energy-norm error ||e - V r||_K^2 / ||e||_K^2, e = K^-1 r.  Keeps the best
+ * parameters seen; *loss_first / *loss_last: mean loss before and after.
+ * Overwrites the context's displacement. */
+TO3D_API to3d_status to3d_mg_train(to3d_ctx* ctx, int32_t nsnap, int32_t steps, double lr,
+                                   uint64_t seed, double* loss_first, double* loss_last);
 
 typedef struct to3d_batch to3d_batch;
 

@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libto3d.so")
 
 F64, BF16_DC, BF16X2_DC, FP16_DC, FP16X2_DC = 0, 1, 2, 3, 4
-JACOBI, CNN_FCG = 0, 1
+JACOBI, CNN_FCG, LMG = 0, 1, 2
 FILTER_SENS, FILTER_DENS = 0, 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error",
           4: "no convergence", 5: "numerical breakdown", 6: "device wait timed out",
@@ -35,7 +35,8 @@ class Params(C.Structure):
                 ("inner_rtol", C.c_double),
                 ("cg_maxit", C.c_int32), ("filter", C.c_int32), ("precision", C.c_int32),
                 ("precond", C.c_int32), ("oc_levels", C.c_int32), ("warm_start", C.c_int32),
-                ("fcg_ref_iters", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("fcg_ref_iters", C.c_int32), ("mg_sweeps", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
 
 
 class IterInfo(C.Structure):
@@ -97,6 +98,12 @@ _SIGS = {
     "to3d_cnn_apply": (I32, [VP, VP, VP, VP, I32]),
     "to3d_cnn_train": (I32, [VP, I32, I32, I32, C.c_double, C.c_uint64, I32, DP, DP]),
     "to3d_cnn_loss_grad": (I32, [VP, VP, VP, VP, I32, VP, C.c_int64, DP]),
+    "to3d_mg_param_count": (I32, [VP, C.POINTER(C.c_int64)]),
+    "to3d_mg_get_params": (I32, [VP, DP, C.c_int64]),
+    "to3d_mg_set_params": (I32, [VP, DP, C.c_int64]),
+    "to3d_mg_levels": (I32, [VP, C.POINTER(I32)]),
+    "to3d_mg_apply": (I32, [VP, VP, VP, VP, I32]),
+    "to3d_mg_train": (I32, [VP, I32, I32, C.c_double, C.c_uint64, DP, DP]),
     "to3d_conv3d_forward": (I32, [I32, I32, I32, I32, I32, I32, VP, VP, VP, VP, I32, VP, VP]),
     "to3d_conv3d_backward": (I32, [I32, I32, I32, I32, I32, I32, VP, VP, VP, VP, VP, VP, VP, VP,
                                    VP]),
@@ -404,6 +411,42 @@ class Context:
         a, b = C.c_double(), C.c_double()
         self._check(self.lib.to3d_cnn_train(self.h, nsnap, per_design, steps, lr, seed, source,
                                             C.byref(a), C.byref(b)), "cnn_train")
+        return a.value, b.value
+
+    # ---- learned multigrid preconditioner (not in the paper)
+    def mg_params(self) -> np.ndarray:
+        n = C.c_int64()
+        self._check(self.lib.to3d_mg_param_count(self.h, C.byref(n)), "mg_param_count")
+        th = np.empty(n.value)
+        self._check(self.lib.to3d_mg_get_params(self.h, th.ctypes.data_as(DP), th.size),
+                    "mg_params")
+        return th
+
+    def set_mg_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        self._check(self.lib.to3d_mg_set_params(self.h, th.ctypes.data_as(DP), th.size),
+                    "set_mg_params")
+
+    def mg_levels(self) -> int:
+        n = I32()
+        self._check(self.lib.to3d_mg_levels(self.h, C.byref(n)), "mg_levels")
+        return n.value
+
+    def mg_apply(self, x, r, z=None):
+        z = np.empty(self.ndof) if z is None else z
+        ax, ar, az = (_need(_Arg(x, np.float64), self.nel, "x"),
+                      _need(_Arg(r, np.float64), self.ndof, "r"),
+                      _need(_Arg(z, np.float64), self.ndof, "z"))
+        dev = _same_kind(ax, ar, az)
+        self._check(self.lib.to3d_mg_apply(self.h, ax.ptr, ar.ptr, az.ptr, dev), "mg_apply")
+        return z
+
+    def mg_train(self, nsnap: int = 8, steps: int = 40, lr: float = 0.05, seed: int = 0):
+        """Learn the multigrid parameters on the current design; returns the
+        mean energy loss before and after."""
+        a, b = C.c_double(), C.c_double()
+        self._check(self.lib.to3d_mg_train(self.h, nsnap, steps, lr, seed, C.byref(a),
+                                           C.byref(b)), "mg_train")
         return a.value, b.value
 
 

@@ -151,6 +151,7 @@ static cudaError_t dalloc(T** p, size_t n) {
 }
 
 static void free_all(to3d_ctx* c) {
+    destroy_mg(c);
     if (c->xphys) cudaFree(c->xphys);
     void* ptrs[] = {c->x, c->xnew, c->E, c->E32, c->ce, c->dc, c->dcf, c->Hs, c->ocq, c->oclo,
                     c->ochi, c->passive, c->nodemask, c->dinv, c->dinv32, c->f, c->ftmp, c->u,
@@ -455,6 +456,7 @@ static to3d_status prepare_operator(to3d_ctx* c, const double* x) {
     c->xop = x;
     launch_simp(c, c->stream, x);
     launch_diag(c, c->stream, c->E);
+    mg_operator_changed(c);
     LK("simp/diag");
     return TO3D_OK;
 }
@@ -496,6 +498,8 @@ static to3d_status solve_current(to3d_ctx* c, const double* f, double fnorm, to3
         launch_fill_zero(c, c->stream, c->u, sizeof(double) * 3 * c->g.nnode);
     to3d_status st;
     if (c->prm.precond == TO3D_CNN_FCG) st = solve_fcg(c, f, fnorm, info);
+    else if (c->prm.precond == TO3D_LMG && c->prm.precision == TO3D_F64) st = solve_fcg(c, f, fnorm, info);
+    else if (c->prm.precond == TO3D_LMG) st = solve_dc_mg(c, f, fnorm, info);
     else if (c->prm.precision == TO3D_F64) st = solve_f64(c, f, fnorm, info);
     else st = solve_dc(c, f, fnorm, info);
     c->have_u = true;
@@ -503,6 +507,11 @@ static to3d_status solve_current(to3d_ctx* c, const double* f, double fnorm, to3
 }
 
 namespace to3d {
+to3d_status true_residual64(to3d_ctx* c, const double* f, double fnorm, double* relres) {
+    return true_residual(c, f, fnorm, relres);
+}
+to3d_status sync_solver_scalars(to3d_ctx* c) { return sync_scalars(c); }
+
 // FP64 Jacobi-PCG continuing from the current u (fallback of flexible CG)
 to3d_status solve64_from_u(to3d_ctx* c, const double* f, double fnorm, to3d_solve_info* info) {
     return solve_f64(c, f, fnorm, info);
@@ -566,7 +575,9 @@ to3d_status to3d_create(const to3d_params* prm, const uint8_t* fixed, const doub
         prm->cg_maxit < 1 || prm->oc_levels < 1 || prm->oc_levels > 5 || prm->precision < 0 ||
         prm->precision > 4 || prm->filter < 0 || prm->filter > 1 || prm->fcg_ref_iters < 0)
         return TO3D_EINVAL;
-    if (prm->precond != TO3D_JACOBI && prm->precond != TO3D_CNN_FCG) return TO3D_EINVAL;
+    if (prm->precond != TO3D_JACOBI && prm->precond != TO3D_CNN_FCG && prm->precond != TO3D_LMG)
+        return TO3D_EINVAL;
+    if (prm->mg_sweeps < 0 || prm->mg_sweeps > 1000) return TO3D_EINVAL;
     {
         // a NaN or Inf load would make every residual test false and end the
         // solves "converged": reject it here

@@ -627,28 +627,48 @@ struct FcgRun {
 // Jacobi-PCG: past 50 iterations, the smallest |r| is 10x above what the
 // context's last plain solve (else params.fcg_ref_iters) would have reached
 // at its average rate.
-static to3d_status fcg_run(to3d_ctx* c, const double* f, int max_its, double rr_stop,
-                           bool stall_check, double rtol, FcgRun* out) {
-    Net* n = net_of(c);
+static to3d_status network_apply(to3d_ctx* c, const double* r, double* z, double) {
+    return cnn_apply(c, r, z);
+}
+
+static FcgIO net_io(Net* n) {
+    FcgIO io;
+    io.z = n->z;
+    io.rprev = n->rprev;
+    io.dots = n->dots;
+    io.dots_h = n->dots_h;
+    io.apply = network_apply;
+    return io;
+}
+
+static to3d_status fcg_run(to3d_ctx* c, const FcgIO& io, const double* f, int max_its,
+                           double rr_stop, bool stall_check, double rtol, FcgRun* out) {
     cudaStream_t s = c->stream;
     const long long ndof = 3 * c->g.nnode;
     to3d_status st;
     FcgRun R;
-    auto network_z = [&](double* rz, double* rr) -> to3d_status {
-        to3d_status e = cnn_apply(c, c->r, n->z);
-        if (e) return e;
-        k_dots<<<blocks(ndof), 256, 0, s>>>(ndof, c->r, n->z, c->r, c->r, c->red, n->dots);
-        CK_RET(cudaMemcpyAsync(n->dots_h, n->dots, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+    double rr_cur = 0.0;
+    // z = M r with the preconditioner of `io`; z = D^-1 r when M gives no
+    // descent direction (r^T z <= 0)
+    auto precond_z = [&](double* rz, double* rr) -> to3d_status {
+        k_dots<<<blocks(ndof), 256, 0, s>>>(ndof, c->r, c->r, nullptr, nullptr, c->red, io.dots);
+        CK_RET(cudaMemcpyAsync(io.dots_h, io.dots, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK_RET(cudaStreamSynchronize(s));
-        *rz = n->dots_h[0];
-        *rr = n->dots_h[1];
+        rr_cur = io.dots_h[0];
+        to3d_status e = io.apply(c, c->r, io.z, rr_cur);
+        if (e) return e;
+        k_dots<<<blocks(ndof), 256, 0, s>>>(ndof, c->r, io.z, c->r, c->r, c->red, io.dots);
+        CK_RET(cudaMemcpyAsync(io.dots_h, io.dots, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+        CK_RET(cudaStreamSynchronize(s));
+        *rz = io.dots_h[0];
+        *rr = io.dots_h[1];
         if (!(*rz > 0.0) && *rr > 0.0) {
             R.jacobi_steps++;
-            k_jacobi_z<<<blocks(c->g.nnode), 256, 0, s>>>(c->g.nnode, c->dinv, c->r, n->z);
-            k_dots<<<blocks(ndof), 256, 0, s>>>(ndof, c->r, n->z, nullptr, nullptr, c->red, n->dots);
-            CK_RET(cudaMemcpyAsync(n->dots_h, n->dots, sizeof(double), cudaMemcpyDeviceToHost, s));
+            k_jacobi_z<<<blocks(c->g.nnode), 256, 0, s>>>(c->g.nnode, c->dinv, c->r, io.z);
+            k_dots<<<blocks(ndof), 256, 0, s>>>(ndof, c->r, io.z, nullptr, nullptr, c->red, io.dots);
+            CK_RET(cudaMemcpyAsync(io.dots_h, io.dots, sizeof(double), cudaMemcpyDeviceToHost, s));
             CK_RET(cudaStreamSynchronize(s));
-            *rz = n->dots_h[0];
+            *rz = io.dots_h[0];
         }
         return TO3D_OK;
     };
@@ -656,8 +676,8 @@ static to3d_status fcg_run(to3d_ctx* c, const double* f, int max_its, double rr_
     launch_matvec64(c, s, c->E, c->u, c->q, false);
     launch_residual64(c, s, f, c->q, c->r, false);
     double rz, rr;
-    if ((st = network_z(&rz, &rr))) return st;
-    CK_RET(cudaMemcpyAsync(c->p, n->z, sizeof(double) * ndof, cudaMemcpyDeviceToDevice, s));
+    if ((st = precond_z(&rz, &rr))) return st;
+    CK_RET(cudaMemcpyAsync(c->p, io.z, sizeof(double) * ndof, cudaMemcpyDeviceToDevice, s));
     double best = rr;
     std::vector<double> marks(1, rr);     // smallest |r|^2 seen, every 50 iterations
     const int ref_its = c->pcg_its_est > 0 ? c->pcg_its_est : c->prm.fcg_ref_iters;
@@ -669,10 +689,10 @@ static to3d_status fcg_run(to3d_ctx* c, const double* f, int max_its, double rr_
             break;
         }
         launch_matvec64(c, s, c->E, c->p, c->q, false);
-        k_dots<<<blocks(ndof), 256, 0, s>>>(ndof, c->p, c->q, c->p, c->r, c->red, n->dots);
-        CK_RET(cudaMemcpyAsync(n->dots_h, n->dots, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+        k_dots<<<blocks(ndof), 256, 0, s>>>(ndof, c->p, c->q, c->p, c->r, c->red, io.dots);
+        CK_RET(cudaMemcpyAsync(io.dots_h, io.dots, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
         CK_RET(cudaStreamSynchronize(s));
-        const double pq = n->dots_h[0], pr = n->dots_h[1];
+        const double pq = io.dots_h[0], pr = io.dots_h[1];
         if (!(pq > 0.0) || !std::isfinite(pq)) {
             R.broke = true;
             R.why = "p^T K p <= 0";
@@ -681,14 +701,14 @@ static to3d_status fcg_run(to3d_ctx* c, const double* f, int max_its, double rr_
         // exact line search along p (alpha = p^T r / p^T K p, not r^T z /
         // p^T K p): the K-norm error decreases in every step even when the
         // preconditioner changes between steps
-        k_fcg_step<<<blocks(ndof), 256, 0, s>>>(ndof, pr / pq, c->u, c->p, c->r, n->rprev, c->q);
+        k_fcg_step<<<blocks(ndof), 256, 0, s>>>(ndof, pr / pq, c->u, c->p, c->r, io.rprev, c->q);
         const double rz_old = rz;
-        if ((st = network_z(&rz, &rr))) return st;
+        if ((st = precond_z(&rz, &rr))) return st;
         // Polak-Ribiere: beta = z^T (r - r_prev) / (z_prev^T r_prev)
-        k_pr_dots<<<blocks(ndof), 256, 0, s>>>(ndof, c->r, n->rprev, n->z, c->red, n->dots);
-        CK_RET(cudaMemcpyAsync(n->dots_h, n->dots, sizeof(double), cudaMemcpyDeviceToHost, s));
+        k_pr_dots<<<blocks(ndof), 256, 0, s>>>(ndof, c->r, io.rprev, io.z, c->red, io.dots);
+        CK_RET(cudaMemcpyAsync(io.dots_h, io.dots, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK_RET(cudaStreamSynchronize(s));
-        const double beta = n->dots_h[0] / rz_old;
+        const double beta = io.dots_h[0] / rz_old;
         ++R.its;
         if (!std::isfinite(rr) || !std::isfinite(rz) || !std::isfinite(beta)) {
             R.broke = true;
@@ -716,7 +736,7 @@ static to3d_status fcg_run(to3d_ctx* c, const double* f, int max_its, double rr_
                 break;
             }
         }
-        k_fcg_dir<<<blocks(ndof), 256, 0, s>>>(ndof, beta, c->p, n->z);
+        k_fcg_dir<<<blocks(ndof), 256, 0, s>>>(ndof, beta, c->p, io.z);
     }
     R.rr = rr;
     *out = R;
@@ -727,18 +747,24 @@ static to3d_status fcg_run(to3d_ctx* c, const double* f, int max_its, double rr_
 static to3d_status fcg_run_iters(to3d_ctx* c, const double* f, int iters) {
     launch_fill_zero(c, c->stream, c->u, sizeof(double) * 3 * c->g.nnode);
     FcgRun R;
-    return fcg_run(c, f, iters, 0.0, false, 0.0, &R);
+    return fcg_run(c, net_io(net_of(c)), f, iters, 0.0, false, 0.0, &R);
 }
 
 // Flexible CG with the network as preconditioner; Jacobi-PCG fallback.
 to3d_status solve_fcg(to3d_ctx* c, const double* f, double fnorm, to3d_solve_info* info) {
-    Net* n = net_of(c);
-    if (!n || !n->trained) return set_err(c, TO3D_ESTATE, "learned preconditioner not trained");
+    FcgIO io;
+    to3d_status st;
+    if (c->prm.precond == TO3D_LMG) {
+        if ((st = mg_fcg_io(c, &io))) return st;
+    } else {
+        Net* n = net_of(c);
+        if (!n || !n->trained) return set_err(c, TO3D_ESTATE, "learned preconditioner not trained");
+        io = net_io(n);
+    }
     cudaStream_t s = c->stream;
     const double tol = c->prm.cg_rtol;
-    to3d_status st;
     FcgRun R;
-    if ((st = fcg_run(c, f, c->prm.cg_maxit, 0.25 * tol * tol * fnorm * fnorm, true, tol, &R)))
+    if ((st = fcg_run(c, io, f, c->prm.cg_maxit, 0.25 * tol * tol * fnorm * fnorm, true, tol, &R)))
         return st;
     bool fellback = R.broke || R.its >= c->prm.cg_maxit;
     if (c->trace)

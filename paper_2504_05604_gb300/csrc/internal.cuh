@@ -153,6 +153,7 @@ struct to3d_ctx {
     void* dcctl = nullptr;                // device control block of the graph's solver
     void* dcctl_h = nullptr;              // pinned copy of it
     void* cnn = nullptr;                  // learned preconditioner (network, workspaces)
+    void* mg = nullptr;                   // learned multigrid preconditioner (levels, buffers)
 };
 
 // ---------------------------------------------------------------- launchers
@@ -191,6 +192,10 @@ void launch_mask_copy(to3d_ctx* c, cudaStream_t s, const double* src, double* ds
 
 // matvec_tc.cu
 void launch_matvec_tc(to3d_ctx* c, cudaStream_t s, int prec, bool fused, int parity);
+void launch_matvec_tc_io(to3d_ctx* c, cudaStream_t s, int prec, bool fused, const CUtensorMap& tr,
+                         const CUtensorMap& tp, const CUtensorMap& td, float* p_new, float* q,
+                         SolverScalars* ss);
+bool encode_vec_map(to3d_ctx* c, CUtensorMap* map, const float* base, int comps);
 void launch_aos_to_soa(to3d_ctx* c, cudaStream_t s, const float* in, float* out);
 void launch_soa_to_aos(to3d_ctx* c, cudaStream_t s, const float* q, const float* p, float* y);
 void init_tc_attributes();
@@ -215,6 +220,23 @@ to3d_status solve64_rtol(to3d_ctx* c, const double* f, double fnorm, double rtol
                          to3d_solve_info* info);
 to3d_status solve64_from_u(to3d_ctx* c, const double* f, double fnorm, to3d_solve_info* info);
 void destroy_cnn(to3d_ctx* c);
+// flexible CG (cnn.cu) with a preconditioner supplied by its owner
+struct FcgIO {
+    double *z = nullptr, *rprev = nullptr, *dots = nullptr, *dots_h = nullptr;
+    // z = M r for the FP64 residual r with |r|^2 = rr
+    to3d_status (*apply)(to3d_ctx* c, const double* r, double* z, double rr) = nullptr;
+};
+to3d_status true_residual64(to3d_ctx* c, const double* f, double fnorm, double* relres);
+to3d_status sync_solver_scalars(to3d_ctx* c);
+void launch_pcg32_update_mode(to3d_ctx* c, cudaStream_t s, const float* p_new, int jacobi_beta);
+void launch_dots64(to3d_ctx* c, cudaStream_t s, long long n, const double* a, const double* b,
+                   const double* cc, const double* d, double* out_dev);
+// mg.cu
+void destroy_mg(to3d_ctx* c);
+void mg_operator_changed(to3d_ctx* c);
+to3d_status mg_apply64(to3d_ctx* c, const double* r, double* z, double rnorm);
+to3d_status mg_fcg_io(to3d_ctx* c, FcgIO* io);
+to3d_status solve_dc_mg(to3d_ctx* c, const double* f, double fnorm, to3d_solve_info* info);
 constexpr int kElementThreads = 256;   // threads per block of the element kernels
 void launch_filter(to3d_ctx* c, cudaStream_t s, int mode, const double* a, const double* b,
                    double* out);

@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, TC_CTAS_PER_SM)
     constexpr int ND = SPLIT ? 2 : 4;
     using L = TcSmemWs<NSL, NMMA>;
     constexpr int NS = L::NS;
-    if (FUSED && a.ss->done) return;
+    if (a.ss && a.ss->done) return;
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -797,26 +797,40 @@ bool prepare_tc_operands(to3d_ctx* c) {
 }
 
 template <int PREC, bool FUSED, bool SPLIT>
-static void launch_one(to3d_ctx* c, cudaStream_t s, const TcArgs& a, const CUtensorMap& tp) {
+static void launch_one(to3d_ctx* c, cudaStream_t s, const TcArgs& a, const CUtensorMap& tr,
+                       const CUtensorMap& tp, const CUtensorMap& td) {
     constexpr int NSL = (PREC == 2 || PREC == 4) ? 2 : 1;
     const int per_sm = TC_CTAS_PER_SM;
     const int grid = a.ntiles < c->tc_grid * per_sm ? a.ntiles : c->tc_grid * per_sm;
     k_matvec_tc<PREC, FUSED, SPLIT><<<grid, TC_ROLE_THREADS, TcSmemWs<NSL, SPLIT ? 64 : 32>::BYTES, s>>>(
-        a, c->tm_r, tp, c->tm_d, c->tm_e);
+        a, tr, tp, td, c->tm_e);
     c->launches++;
 }
 
 template <bool FUSED, bool SPLIT>
-static void launch_prec(to3d_ctx* c, cudaStream_t s, const TcArgs& a, int prec, const CUtensorMap& tp) {
-    if (prec == TO3D_BF16X2_DC) launch_one<2, FUSED, SPLIT>(c, s, a, tp);
-    else if (prec == TO3D_FP16_DC) launch_one<3, FUSED, SPLIT>(c, s, a, tp);
-    else if (prec == TO3D_FP16X2_DC) launch_one<4, FUSED, SPLIT>(c, s, a, tp);
-    else launch_one<1, FUSED, SPLIT>(c, s, a, tp);
+static void launch_prec(to3d_ctx* c, cudaStream_t s, const TcArgs& a, int prec, const CUtensorMap& tr,
+                        const CUtensorMap& tp, const CUtensorMap& td) {
+    if (prec == TO3D_BF16X2_DC) launch_one<2, FUSED, SPLIT>(c, s, a, tr, tp, td);
+    else if (prec == TO3D_FP16_DC) launch_one<3, FUSED, SPLIT>(c, s, a, tr, tp, td);
+    else if (prec == TO3D_FP16X2_DC) launch_one<4, FUSED, SPLIT>(c, s, a, tr, tp, td);
+    else launch_one<1, FUSED, SPLIT>(c, s, a, tr, tp, td);
 }
 
 // Fused: p_old is p32b (parity 0) or p32a (parity 1), p_new the other one.
 // Plain: the input is p32a (padded SoA), the output q32.
 void launch_matvec_tc(to3d_ctx* c, cudaStream_t s, int prec, bool fused, int parity) {
+    const CUtensorMap& tp = fused ? (parity ? c->tm_pa : c->tm_pb) : c->tm_pa;
+    launch_matvec_tc_io(c, s, prec, fused, c->tm_r, tp, c->tm_d,
+                        fused ? (parity ? c->p32b : c->p32a) : nullptr, c->q32, fused ? c->ss : nullptr);
+}
+
+// General form: the maps of r (fused only), p (fused: p_old; plain: the
+// input) and the per-node scaling d (fused only), the outputs p_new (fused
+// only) and q.  `ss` (may be null in plain mode): the kernel returns at once
+// when ss->done is set.
+void launch_matvec_tc_io(to3d_ctx* c, cudaStream_t s, int prec, bool fused, const CUtensorMap& tr,
+                         const CUtensorMap& tp, const CUtensorMap& td, float* p_new, float* q,
+                         SolverScalars* ss) {
     const Grid& g = c->g;
     TcArgs a;
     a.g = g;
@@ -834,19 +848,24 @@ void launch_matvec_tc(to3d_ctx* c, cudaStream_t s, int prec, bool fused, int par
     const int nmma = c->tc_split ? 64 : 32;
     a.Bglob = c->tcB + ((prec == TO3D_FP16_DC || prec == TO3D_FP16X2_DC) ? nmma * 64 : 0);
     a.E32 = c->E32;
-    a.p_new = fused ? (parity ? c->p32b : c->p32a) : nullptr;
-    a.q = c->q32;
+    a.p_new = p_new;
+    a.q = q;
     a.red = c->red;
-    a.ss = c->ss;
+    a.ss = ss;
     a.err = c->dev_err;
-    const CUtensorMap& tp = fused ? (parity ? c->tm_pa : c->tm_pb) : c->tm_pa;
     if (fused) {
-        if (c->tc_split) launch_prec<true, true>(c, s, a, prec, tp);
-        else launch_prec<true, false>(c, s, a, prec, tp);
+        if (c->tc_split) launch_prec<true, true>(c, s, a, prec, tr, tp, td);
+        else launch_prec<true, false>(c, s, a, prec, tr, tp, td);
     } else {
-        if (c->tc_split) launch_prec<false, true>(c, s, a, prec, tp);
-        else launch_prec<false, false>(c, s, a, prec, tp);
+        if (c->tc_split) launch_prec<false, true>(c, s, a, prec, tr, tp, td);
+        else launch_prec<false, false>(c, s, a, prec, tr, tp, td);
     }
+}
+
+// TMA map of a padded SoA vector of context c (3 components) or of a
+// per-node array (1 component), for launch_matvec_tc_io.
+bool encode_vec_map(to3d_ctx* c, CUtensorMap* map, const float* base, int comps) {
+    return encode_map(c, map, base, comps);
 }
 
 void launch_aos_to_soa(to3d_ctx* c, cudaStream_t s, const float* in, float* out) {

@@ -1,0 +1,854 @@
+// Learned multigrid preconditioner for the state equation K u = f.
+//
+// The paper solves K U = F with a sparse direct solver (Section 2.2); the
+// library solves it iteratively, and Jacobi-preconditioned CG needs thousands
+// of iterations on fine SIMP grids.  This file builds a geometric multigrid
+// V-cycle on the same operator K = sum_e E_e KE whose free parameters are
+// learned from the method's own residuals:
+//
+//   hierarchy   level l+1 halves every element count of level l, rounding
+//               up; coarse node C sits on fine node 2C; a coarse dof is
+//               clamped when the fine dof at 2C is.  Each coarse level is a
+//               full context of its own (same element, same tensor-core
+//               kernel), created once per design grid.
+//   coarse K    rediscretised: coarse element modulus s_l (mean over the 8
+//               child slots of E^q_l)^(1/q_l), missing children 0 (s = 2 and
+//               any q give the Galerkin operator for a uniform modulus).
+//   transfer    trilinear prolongation, restriction its transpose.
+//   smoother    damped Jacobi with weight w_l, one sweep before and one
+//               after the coarse correction; `sweeps` sweeps on the coarsest
+//               level.
+//   learned     theta = (w_g for g = 0..3, q_g and s_g for g = 1..3), group g
+//               = min(level, 3), so parameters learned on one grid size apply
+//               to any other.  Training minimises the energy-norm error that
+//               one application leaves, ||e - V r||_K^2 / ||e||_K^2 with
+//               e = K^-1 r, over residual snapshots of the context's own
+//               design, by Adam on central-difference gradients.
+//
+// The cycle runs in FP32 on the padded structure-of-arrays vectors of each
+// level, every operator application on the tensor cores (the context's
+// operand form).  It is linear in its input and symmetric up to that
+// rounding, so it serves flexible CG in FP64 (TO3D_F64) and an FP32 inner
+// CG inside the FP64 defect correction (the *_DC forms).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+#include "reduce.cuh"
+
+#define MG_CK(call)                                             \
+    do {                                                        \
+        cudaError_t _e = (call);                                \
+        if (_e != cudaSuccess) return cuda_check(c, _e, #call); \
+    } while (0)
+
+namespace to3d {
+namespace mg {
+
+constexpr int kGroups = 4;                          // level 0, 1, 2, >= 3
+constexpr int kParams = kGroups + 2 * (kGroups - 1);
+constexpr int kMaxLevels = 12;
+constexpr int kThreads = 256;
+
+struct Level {
+    to3d_ctx* ctx = nullptr;     // level 0: the owning context (not owned here)
+    float* z = nullptr;          // cycle solution (padded SoA, 3 vol)
+    float* t = nullptr;          // operator output
+    CUtensorMap tm_z;
+};
+
+struct Snap {
+    double* r = nullptr;         // residual (AoS FP64, dofs)
+    double rn = 0.0;             // |r|
+    double rte = 0.0;            // r^T K^-1 r
+};
+
+struct Mg {
+    std::vector<Level> lv;
+    double theta[kParams];
+    float* wdev = nullptr;            // smoothing weight per level (device)
+    int sweeps = 16;
+    int prec = TO3D_BF16_DC;
+    cudaGraphExec_t cycle = nullptr;  // ctx->r32 -> lv[0].z, captured
+    long long cycle_launches = 0;     // kernels in one cycle
+    bool params_dirty = true;         // coarse moduli / weights not set up for the current operator
+    double* z64 = nullptr;            // FP64 flexible-CG buffers
+    double* rprev = nullptr;
+    double* dots = nullptr;
+    double* dots_h = nullptr;
+    float* ones = nullptr;            // per-node scaling 1 (fused direction p = z + beta p)
+    CUtensorMap tm_ones;
+    cudaGraphExec_t pcg = nullptr;    // chunk of inner MG-PCG iterations
+    int pcg_prec = -1, pcg_n = 0;
+    std::vector<Snap> snaps;
+    bool trained = false;
+};
+
+static int group(int l) { return l < kGroups - 1 ? l : kGroups - 1; }
+static double w_of(const Mg* m, int l) { return m->theta[group(l)]; }
+static double q_of(const Mg* m, int l) { return m->theta[kGroups + group(l) - 1]; }
+static double s_of(const Mg* m, int l) { return m->theta[2 * kGroups - 1 + group(l) - 1]; }
+
+static void default_theta(double* th) {
+    for (int g = 0; g < kGroups; ++g) th[g] = 0.5;
+    for (int g = 1; g < kGroups; ++g) {
+        th[kGroups + g - 1] = 1.0;
+        th[2 * kGroups - 1 + g - 1] = 2.0;
+    }
+}
+
+static bool theta_valid(const double* th) {
+    for (int g = 0; g < kGroups; ++g)
+        if (!(th[g] > 0.0 && th[g] < 1.0)) return false;
+    for (int g = 1; g < kGroups; ++g) {
+        const double q = th[kGroups + g - 1], s = th[2 * kGroups - 1 + g - 1];
+        if (!(q >= 0.125 && q <= 8.0) || !(s > 0.0 && s <= 64.0)) return false;
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------ kernels
+__device__ __forceinline__ bool skip(const SolverScalars* ss) { return ss && ss->done; }
+
+// z = w D^-1 b (first smoothing sweep, from z = 0); clamped dofs and pads 0
+__global__ void k_jacobi0(long long vol, const float* __restrict__ b, const float* __restrict__ dinv,
+                          const uint8_t* __restrict__ maskp, const float* __restrict__ wdev, int l,
+                          float* __restrict__ z, const SolverScalars* ss) {
+    if (skip(ss)) return;
+    const float w = wdev[l];
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < vol;
+         n += (long long)gridDim.x * blockDim.x) {
+        const float d = w * dinv[n];
+        const uint8_t m = maskp[n];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) z[c * vol + n] = ((m >> c) & 1) ? 0.f : d * b[c * vol + n];
+    }
+}
+
+// z += w D^-1 (b - t), t = K z
+__global__ void k_jacobi(long long vol, const float* __restrict__ b, const float* __restrict__ t,
+                         const float* __restrict__ dinv, const uint8_t* __restrict__ maskp,
+                         const float* __restrict__ wdev, int l, float* __restrict__ z,
+                         const SolverScalars* ss) {
+    if (skip(ss)) return;
+    const float w = wdev[l];
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < vol;
+         n += (long long)gridDim.x * blockDim.x) {
+        const float d = w * dinv[n];
+        const uint8_t m = maskp[n];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long i = c * vol + n;
+            z[i] = ((m >> c) & 1) ? 0.f : fmaf(d, b[i] - t[i], z[i]);
+        }
+    }
+}
+
+// b_c = R (b_f - t_f): each coarse node gathers the 27 fine nodes 2C + d,
+// weights prod (1 - |d| / 2); clamped dofs of either grid contribute 0
+__global__ void k_restrict(const Grid gf, int pxf, long long volf, const float* __restrict__ bf,
+                           const float* __restrict__ tf, const uint8_t* __restrict__ maskf,
+                           const Grid gc, int pxc, long long volc, const uint8_t* __restrict__ maskc,
+                           float* __restrict__ bc, const SolverScalars* ss) {
+    if (skip(ss)) return;
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= gc.nnode) return;
+    const int i = n % gc.nx, j = (n / gc.nx) % gc.ny, k = n / ((long long)gc.nx * gc.ny);
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int dk = -1; dk <= 1; ++dk) {
+        const int fk = 2 * k + dk;
+        if (fk < 0 || fk >= gf.nz) continue;
+        const float wk = dk ? 0.5f : 1.f;
+        for (int dj = -1; dj <= 1; ++dj) {
+            const int fj = 2 * j + dj;
+            if (fj < 0 || fj >= gf.ny) continue;
+            const float wj = wk * (dj ? 0.5f : 1.f);
+            for (int di = -1; di <= 1; ++di) {
+                const int fi = 2 * i + di;
+                if (fi < 0 || fi >= gf.nx) continue;
+                const float wt = wj * (di ? 0.5f : 1.f);
+                const long long p = fi + (long long)pxf * (fj + (long long)gf.ny * fk);
+                const uint8_t m = maskf[p];
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    if (!((m >> c) & 1)) acc[c] = fmaf(wt, bf[c * volf + p] - tf[c * volf + p], acc[c]);
+            }
+        }
+    }
+    const long long pc = i + (long long)pxc * (j + (long long)gc.ny * k);
+    const uint8_t mc = maskc[pc];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) bc[c * volc + pc] = ((mc >> c) & 1) ? 0.f : acc[c];
+}
+
+// z_f += P z_c (trilinear), clamped fine dofs untouched (they stay 0)
+__global__ void k_prolong(const Grid gf, int pxf, long long volf, const uint8_t* __restrict__ maskf,
+                          float* __restrict__ zf, const Grid gc, int pxc, long long volc,
+                          const float* __restrict__ zc, const SolverScalars* ss) {
+    if (skip(ss)) return;
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= gf.nnode) return;
+    const int i = n % gf.nx, j = (n / gf.nx) % gf.ny, k = n / ((long long)gf.nx * gf.ny);
+    const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
+    const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
+    const float wi = (i & 1) ? 0.5f : 1.f, wj = (j & 1) ? 0.5f : 1.f, wk = (k & 1) ? 0.5f : 1.f;
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < nk; ++a)
+        for (int bb = 0; bb < nj; ++bb)
+            for (int cc = 0; cc < ni; ++cc) {
+                const long long p = (i0 + cc) + (long long)pxc * ((j0 + bb) + (long long)gc.ny * (k0 + a));
+                const float w = wi * wj * wk;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc[c] = fmaf(w, zc[c * volc + p], acc[c]);
+            }
+    const long long pf = i + (long long)pxf * (j + (long long)gf.ny * k);
+    const uint8_t m = maskf[pf];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        if (!((m >> c) & 1)) zf[c * volf + pf] += acc[c];
+}
+
+// coarse moduli: s (sum over the 8 child slots of E^q / 8)^(1/q), missing 0
+__global__ void k_coarsen(const Grid gf, const double* __restrict__ Ef, const Grid gc, double q,
+                          double s, double* __restrict__ Ec, float* __restrict__ E32c, int pexc) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= gc.nel) return;
+    const int i = e % gc.nelx, j = (e / gc.nelx) % gc.nely, k = e / ((long long)gc.nelx * gc.nely);
+    double acc = 0.0;
+    for (int c = 0; c < 2; ++c)
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a) {
+                const int fi = 2 * i + a, fj = 2 * j + b, fk = 2 * k + c;
+                if (fi < gf.nelx && fj < gf.nely && fk < gf.nelz) {
+                    const double v = Ef[elem_id(gf, fi, fj, fk)];
+                    acc += (q == 1.0) ? v : pow(v, q);
+                }
+            }
+    const double m = acc / 8.0;
+    const double v = s * ((q == 1.0) ? m : pow(m, 1.0 / q));
+    Ec[e] = v;
+    E32c[i + (long long)pexc * (j + (long long)gc.nely * k)] = (float)v;
+}
+
+// b = scale r64 (AoS FP64 -> padded SoA FP32), clamped dofs 0
+__global__ void k_in(const Grid g, int px, long long vol, const double* __restrict__ r64, double scale,
+                     const uint8_t* __restrict__ nodemask, float* __restrict__ b) {
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < g.nnode;
+         n += (long long)gridDim.x * blockDim.x) {
+        const long long p = (n % g.nx) + (long long)px * (n / g.nx);
+        const uint8_t m = nodemask[n];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) b[c * vol + p] = ((m >> c) & 1) ? 0.f : (float)(r64[3 * n + c] * scale);
+    }
+}
+
+// z64 = z / scale (padded SoA FP32 -> AoS FP64)
+__global__ void k_out(const Grid g, int px, long long vol, const float* __restrict__ z, double inv_scale,
+                      double* __restrict__ z64) {
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < g.nnode;
+         n += (long long)gridDim.x * blockDim.x) {
+        const long long p = (n % g.nx) + (long long)px * (n / g.nx);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) z64[3 * n + c] = (double)z[c * vol + p] * inv_scale;
+    }
+}
+
+__global__ void k_fill(long long n, float v, float* __restrict__ a) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
+// Inner MG-PCG, after the cycle z = V r: rz = r.z and z.q_old give the
+// Polak-Ribiere coefficient beta = z_new.(r_new - r_old) / rz_old
+// = -alpha z_new.q_old / rz_old (0 on the first step of a segment).
+__global__ void k_pcg_dots(long long vol, const float* __restrict__ r, const float* __restrict__ z,
+                           const float* __restrict__ q, const Reducer red, SolverScalars* ss) {
+    if (ss->done) return;
+    __shared__ double sh[64];
+    __shared__ double out[2];
+    double rz = 0.0, zq = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 3 * vol;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float zv = z[i];
+        rz = fma((double)r[i], (double)zv, rz);
+        zq = fma((double)zv, (double)q[i], zq);
+    }
+    double v[2] = {rz, zq};
+    if (grid_sum<2>(red, v, sh, out) && threadIdx.x == 0) {
+        const double rzn = out[0];
+        const bool first = ss->pad0 != 0;
+        const double beta = first ? 0.0 : -ss->alpha * out[1] / ss->rz;
+        ss->pad0 = 0;
+        ss->beta = beta;
+        ss->zcoef = 1.0;
+        ss->rz = rzn;
+        if (!(rzn > 0.0) || !isfinite(rzn) || !isfinite(beta)) {
+            ss->status = TO3D_ENUMERIC;
+            ss->done = 1;
+        }
+    }
+}
+
+// Segment start: r32 = scale r64 (masked), d = 0, p_old = 0, q = 0; |r32|^2
+__global__ void k_pcg_init(const Grid g, int px, long long vol, const double* __restrict__ r64, double scale,
+                           const uint8_t* __restrict__ nodemask, float* __restrict__ r32,
+                           float* __restrict__ d32, float* __restrict__ p_old, float* __restrict__ q,
+                           const Reducer red, SolverScalars* ss) {
+    __shared__ double sh[32];
+    __shared__ double out[1];
+    double rr = 0.0;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < g.nnode;
+         n += (long long)gridDim.x * blockDim.x) {
+        const long long p = (n % g.nx) + (long long)px * (n / g.nx);
+        const uint8_t m = nodemask[n];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float v = ((m >> c) & 1) ? 0.f : (float)(r64[3 * n + c] * scale);
+            r32[c * vol + p] = v;
+            d32[c * vol + p] = 0.f;
+            p_old[c * vol + p] = 0.f;
+            q[c * vol + p] = 0.f;
+            rr = fma((double)v, (double)v, rr);
+        }
+    }
+    double v[1] = {rr};
+    if (grid_sum<1>(red, v, sh, out) && threadIdx.x == 0) {
+        ss->rr = out[0];
+        ss->beta = 0.0;
+        ss->zcoef = 1.0;
+        ss->pad0 = 1;        // the next k_pcg_dots starts a new direction sequence
+        if (!isfinite(out[0])) {
+            ss->status = TO3D_ENUMERIC;
+            ss->done = 1;
+        } else if (out[0] <= ss->tol2) {
+            ss->done = 1;
+        }
+    }
+}
+
+static unsigned nblocks(long long n) {
+    long long b = (n + kThreads - 1) / kThreads;
+    if (b > 152 * 8) b = 152 * 8;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace mg
+
+using namespace mg;
+
+static Mg* mg_of(to3d_ctx* c) { return (Mg*)c->mg; }
+
+void destroy_mg(to3d_ctx* c) {
+    Mg* m = mg_of(c);
+    if (!m) return;
+    if (m->cycle) cudaGraphExecDestroy(m->cycle);
+    if (m->pcg) cudaGraphExecDestroy(m->pcg);
+    for (size_t l = 0; l < m->lv.size(); ++l) {
+        cudaFree(m->lv[l].z);
+        cudaFree(m->lv[l].t);
+        if (l > 0) to3d_destroy(m->lv[l].ctx);
+    }
+    for (auto& s : m->snaps) cudaFree(s.r);
+    void* ptrs[] = {m->wdev, m->z64, m->rprev, m->dots, m->ones};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (m->dots_h) cudaFreeHost(m->dots_h);
+    delete m;
+    c->mg = nullptr;
+}
+
+// Build the level hierarchy once per context (coarse contexts, buffers, maps).
+static to3d_status ensure_mg(to3d_ctx* c) {
+    if (c->mg) return TO3D_OK;
+    Mg* m = new (std::nothrow) Mg();
+    if (!m) return set_err(c, TO3D_ENOMEM, "multigrid");
+    c->mg = m;
+    default_theta(m->theta);
+    m->sweeps = c->prm.mg_sweeps > 0 ? c->prm.mg_sweeps : 16;
+    m->prec = c->prm.precision == TO3D_F64 ? TO3D_BF16_DC : c->prm.precision;
+    // clamp masks on the host, level by level
+    const Grid& g0 = c->g;
+    std::vector<uint8_t> mask(g0.nnode);
+    MG_CK(cudaMemcpy(mask.data(), c->nodemask, g0.nnode, cudaMemcpyDeviceToHost));
+    Level L0;
+    L0.ctx = c;
+    m->lv.push_back(L0);
+    int dims[3] = {g0.nelx, g0.nely, g0.nelz};
+    while ((int)m->lv.size() < kMaxLevels &&
+           std::max(dims[0], std::max(dims[1], dims[2])) > 4 &&
+           std::min(dims[0], std::min(dims[1], dims[2])) >= 2) {
+        const int fx = dims[0] + 1, fy = dims[1] + 1, fz = dims[2] + 1;
+        int cd[3] = {(dims[0] + 1) / 2, (dims[1] + 1) / 2, (dims[2] + 1) / 2};
+        const int cx = cd[0] + 1, cy = cd[1] + 1, cz = cd[2] + 1;
+        std::vector<uint8_t> fixed(3LL * cx * cy * cz, 0), cmask((size_t)cx * cy * cz, 0);
+        for (int k = 0; k < cz; ++k)
+            for (int j = 0; j < cy; ++j)
+                for (int i = 0; i < cx; ++i) {
+                    if (2 * i >= fx || 2 * j >= fy || 2 * k >= fz) continue;
+                    const uint8_t fm = mask[(size_t)(2 * i) + (size_t)fx * ((size_t)(2 * j) + (size_t)fy * (2 * k))];
+                    const size_t n = i + (size_t)cx * (j + (size_t)cy * k);
+                    cmask[n] = fm;
+                    for (int cc = 0; cc < 3; ++cc) fixed[3 * n + cc] = (fm >> cc) & 1;
+                }
+        std::vector<double> load(fixed.size(), 0.0);
+        to3d_params p = c->prm;
+        p.nelx = cd[0];
+        p.nely = cd[1];
+        p.nelz = cd[2];
+        p.precond = TO3D_JACOBI;
+        p.filter = TO3D_FILTER_SENS;
+        p.precision = m->prec;
+        p.rmin = 1.5;
+        Level Lc;
+        to3d_status st = to3d_create(&p, fixed.data(), load.data(), nullptr, c->stream, &Lc.ctx);
+        if (st) return set_err(c, st, "multigrid coarse level");
+        m->lv.push_back(Lc);
+        mask.swap(cmask);
+        dims[0] = cd[0];
+        dims[1] = cd[1];
+        dims[2] = cd[2];
+    }
+    for (auto& L : m->lv) {
+        const size_t bytes = sizeof(float) * 3 * L.ctx->vol;
+        MG_CK(cudaMalloc(&L.z, bytes));
+        MG_CK(cudaMalloc(&L.t, bytes));
+        MG_CK(cudaMemset(L.z, 0, bytes));
+        MG_CK(cudaMemset(L.t, 0, bytes));
+        if (!encode_vec_map(L.ctx, &L.tm_z, L.z, 3)) return set_err(c, TO3D_ECUDA, "multigrid TMA map");
+    }
+    const long long ndof = 3 * g0.nnode;
+    MG_CK(cudaMalloc(&m->wdev, sizeof(float) * kMaxLevels));
+    MG_CK(cudaMalloc(&m->z64, sizeof(double) * ndof));
+    MG_CK(cudaMalloc(&m->rprev, sizeof(double) * ndof));
+    MG_CK(cudaMalloc(&m->dots, sizeof(double) * 4));
+    MG_CK(cudaMallocHost(&m->dots_h, sizeof(double) * 4));
+    MG_CK(cudaMalloc(&m->ones, sizeof(float) * c->vol));
+    k_fill<<<nblocks(c->vol), kThreads, 0, c->stream>>>(c->vol, 1.f, m->ones);
+    if (!encode_vec_map(c, &m->tm_ones, m->ones, 1)) return set_err(c, TO3D_ECUDA, "multigrid TMA map");
+    MG_CK(cudaStreamSynchronize(c->stream));
+    m->params_dirty = true;
+    return TO3D_OK;
+}
+
+// Coarse moduli, diagonals and smoothing weights for the fine moduli c->E
+// (c->dinv32 must already belong to them).
+static to3d_status setup_levels(to3d_ctx* c) {
+    Mg* m = mg_of(c);
+    cudaStream_t s = c->stream;
+    float w[kMaxLevels];
+    for (int l = 0; l < kMaxLevels; ++l) w[l] = (float)w_of(m, l);
+    MG_CK(cudaMemcpyAsync(m->wdev, w, sizeof(w), cudaMemcpyHostToDevice, s));
+    for (size_t l = 1; l < m->lv.size(); ++l) {
+        to3d_ctx* f = m->lv[l - 1].ctx;
+        to3d_ctx* k = m->lv[l].ctx;
+        k_coarsen<<<(unsigned)((k->g.nel + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+            f->g, f->E, k->g, q_of(m, (int)l), s_of(m, (int)l), k->E, k->E32, k->pex);
+        launch_diag(k, s, k->E);
+        c->launches += 2;
+    }
+    m->params_dirty = false;
+    return launch_check(c, "multigrid set-up");
+}
+
+// One V-cycle from level l: b (padded SoA of level l) -> lv[l].z.
+static void cycle_launch(to3d_ctx* c, Mg* m, cudaStream_t s, size_t l, const float* b,
+                         SolverScalars* ss) {
+    Level& L = m->lv[l];
+    to3d_ctx* k = L.ctx;
+    const long long vol = k->vol;
+    auto op = [&]() {
+        launch_matvec_tc_io(k, s, m->prec, false, k->tm_r, L.tm_z, k->tm_d, nullptr, L.t, ss);
+        if (k != c) c->launches++;
+    };
+    k_jacobi0<<<nblocks(vol), kThreads, 0, s>>>(vol, b, k->dinv32, k->maskp, m->wdev, (int)l, L.z, ss);
+    c->launches++;
+    if (l + 1 == m->lv.size()) {
+        for (int i = 1; i < m->sweeps; ++i) {
+            op();
+            k_jacobi<<<nblocks(vol), kThreads, 0, s>>>(vol, b, L.t, k->dinv32, k->maskp, m->wdev, (int)l,
+                                                      L.z, ss);
+            c->launches++;
+        }
+        return;
+    }
+    Level& C = m->lv[l + 1];
+    to3d_ctx* kc = C.ctx;
+    op();
+    k_restrict<<<(unsigned)((kc->g.nnode + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        k->g, k->px, vol, b, L.t, k->maskp, kc->g, kc->px, kc->vol, kc->maskp, kc->r32, ss);
+    c->launches++;
+    cycle_launch(c, m, s, l + 1, kc->r32, ss);
+    k_prolong<<<(unsigned)((k->g.nnode + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        k->g, k->px, vol, k->maskp, L.z, kc->g, kc->px, kc->vol, C.z, ss);
+    c->launches++;
+    op();
+    k_jacobi<<<nblocks(vol), kThreads, 0, s>>>(vol, b, L.t, k->dinv32, k->maskp, m->wdev, (int)l, L.z, ss);
+    c->launches++;
+}
+
+// Make sure the hierarchy belongs to the current fine operator.
+static to3d_status ready(to3d_ctx* c) {
+    to3d_status st = ensure_mg(c);
+    if (st) return st;
+    Mg* m = mg_of(c);
+    if (m->params_dirty) return setup_levels(c);
+    return TO3D_OK;
+}
+
+// Mark the hierarchy stale (the fine moduli changed).
+void mg_operator_changed(to3d_ctx* c) {
+    Mg* m = mg_of(c);
+    if (m) m->params_dirty = true;
+}
+
+// z = V r for FP64 AoS vectors (r unscaled); uses ctx->r32 as the cycle input.
+to3d_status mg_apply64(to3d_ctx* c, const double* r, double* z, double rnorm) {
+    to3d_status st = ready(c);
+    if (st) return st;
+    Mg* m = mg_of(c);
+    cudaStream_t s = c->stream;
+    const double ndof = 3.0 * (double)c->g.nnode;
+    const double scale = rnorm > 0.0 ? std::sqrt(ndof) / rnorm : 1.0;
+    k_in<<<nblocks(c->g.nnode), kThreads, 0, s>>>(c->g, c->px, c->vol, r, scale, c->nodemask, c->r32);
+    c->launches++;
+    if (!m->cycle) {
+        cudaGraph_t gr;
+        MG_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const long long l0 = c->launches;
+        cycle_launch(c, m, c->cap_stream, 0, c->r32, nullptr);
+        MG_CK(cudaStreamEndCapture(c->cap_stream, &gr));
+        MG_CK(cudaGraphInstantiate(&m->cycle, gr, 0));
+        cudaGraphDestroy(gr);
+        m->cycle_launches = c->launches - l0;
+        c->launches = l0;
+    }
+    MG_CK(cudaGraphLaunch(m->cycle, s));
+    c->launches += m->cycle_launches;
+    k_out<<<nblocks(c->g.nnode), kThreads, 0, s>>>(c->g, c->px, c->vol, m->lv[0].z, 1.0 / scale, z);
+    c->launches++;
+    return launch_check(c, "multigrid cycle");
+}
+
+}  // namespace to3d
+
+// ------------------------------------------------------------------ inner MG-PCG
+namespace to3d {
+
+// One inner iteration: z = V r (cycle on ctx->r32), rz and beta, the fused
+// tensor-core kernel p_new = z + beta p_old, q = K p_new, alpha = rz / p.q,
+// then d += alpha p_new, r -= alpha q and |r|^2 (no Jacobi dot).
+static void mgpcg_iter(to3d_ctx* c, Mg* m, cudaStream_t s, int prec, int parity) {
+    cycle_launch(c, m, s, 0, c->r32, c->ss);
+    k_pcg_dots<<<nblocks(3 * c->vol), kThreads, 0, s>>>(c->vol, c->r32, m->lv[0].z, c->q32, c->red,
+                                                        c->ss);
+    c->launches++;
+    float* p_new = parity ? c->p32b : c->p32a;
+    const CUtensorMap& tp = parity ? c->tm_pa : c->tm_pb;
+    launch_matvec_tc_io(c, s, prec, true, m->lv[0].tm_z, tp, m->tm_ones, p_new, c->q32, c->ss);
+    launch_pcg32_update_mode(c, s, p_new, 0);
+}
+
+static to3d_status mgpcg_chunk(to3d_ctx* c, Mg* m, int prec, int n) {
+    if (n == c->chunk) {
+        if (!m->pcg || m->pcg_prec != prec) {
+            if (m->pcg) cudaGraphExecDestroy(m->pcg);
+            m->pcg = nullptr;
+            cudaGraph_t gr;
+            const long long l0 = c->launches;
+            MG_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+            for (int i = 0; i < n; ++i) mgpcg_iter(c, m, c->cap_stream, prec, i & 1);
+            MG_CK(cudaStreamEndCapture(c->cap_stream, &gr));
+            MG_CK(cudaGraphInstantiate(&m->pcg, gr, 0));
+            cudaGraphDestroy(gr);
+            m->pcg_prec = prec;
+            m->pcg_n = (int)(c->launches - l0);
+            c->launches = l0;
+        }
+        MG_CK(cudaGraphLaunch(m->pcg, c->stream));
+        c->launches += m->pcg_n;
+    } else {
+        for (int i = 0; i < n; ++i) mgpcg_iter(c, m, c->stream, prec, i & 1);
+    }
+    return launch_check(c, "multigrid PCG chunk");
+}
+
+// FP64 defect correction around an FP32 inner CG preconditioned by the
+// cycle: each segment scales the true residual to unit RMS, runs the inner
+// CG until its residual has dropped by inner_rtol (or the global target is
+// met), adds the correction to u in FP64 and recomputes f - K u in FP64.
+// The inner CG restarts at every segment (the cycle makes that cheap).
+to3d_status solve_dc_mg(to3d_ctx* c, const double* f, double fnorm, to3d_solve_info* info) {
+    to3d_status st = ready(c);
+    if (st) return st;
+    Mg* m = mg_of(c);
+    const double tol = c->prm.cg_rtol;
+    const double delta = c->prm.inner_rtol;
+    const int prec = c->prm.precision == TO3D_F64 ? TO3D_BF16_DC : c->prm.precision;
+    const long long ndof = 3 * c->g.nnode;
+    int total = 0, outer = 0, status = TO3D_OK, stalls = 0;
+    double relres = 0.0;
+    if ((st = true_residual64(c, f, fnorm, &relres))) return st;
+    while (relres > tol && fnorm > 0.0) {
+        const double rnorm = relres * fnorm;
+        const double scale = std::sqrt((double)ndof) / rnorm;
+        const double t = 0.5 * tol * fnorm * scale;
+        launch_ss_reset(c, c->stream, std::fmax(delta * delta * (double)ndof, t * t),
+                        c->prm.cg_maxit - total);
+        k_pcg_init<<<nblocks(c->g.nnode), kThreads, 0, c->stream>>>(
+            c->g, c->px, c->vol, c->r, scale, c->nodemask, c->r32, c->d32, c->p32b, c->q32, c->red, c->ss);
+        c->launches++;
+        int n = 4, it0 = 0;
+        for (;;) {
+            const int chunk_n = n < c->chunk ? n : c->chunk;
+            if ((st = mgpcg_chunk(c, m, prec, chunk_n))) return st;
+            if ((st = sync_solver_scalars(c))) return st;
+            it0 = c->ss_h->it;
+            if (c->ss_h->done) break;
+            if (n < c->chunk) n *= 2;
+        }
+        (void)it0;
+        const int its = c->ss_h->it;
+        total += its;
+        if (c->ss_h->status == TO3D_ETIMEOUT || c->ss_h->status == TO3D_ENUMERIC) {
+            status = c->ss_h->status;
+            break;
+        }
+        launch_axpy_d32(c, c->stream, 1.0 / scale);
+        const double prev = relres;
+        if ((st = true_residual64(c, f, fnorm, &relres))) return st;
+        if (c->trace)
+            std::fprintf(stderr, "to3d: mg segment %d: %d inner its (total %d), relres %.3e -> %.3e\n",
+                         outer, its, total, prev, relres);
+        if (relres <= tol) break;
+        ++outer;
+        if (total >= c->prm.cg_maxit || outer >= 1000) {
+            status = TO3D_ENOCONV;
+            break;
+        }
+        if (relres > 0.5 * prev && ++stalls > 20) {
+            status = TO3D_ENOCONV;
+            break;
+        }
+    }
+    if (info) {
+        info->iters = total;
+        info->outer = outer + 1;
+        info->status = status;
+        info->relres = relres;
+    }
+    return TO3D_OK;
+}
+
+// Buffers and preconditioner of flexible CG with the cycle.
+static to3d_status mg_apply_fcg(to3d_ctx* c, const double* r, double* z, double rr) {
+    return mg_apply64(c, r, z, std::sqrt(rr));
+}
+
+to3d_status mg_fcg_io(to3d_ctx* c, FcgIO* io) {
+    to3d_status st = ready(c);
+    if (st) return st;
+    Mg* m = mg_of(c);
+    io->z = m->z64;
+    io->rprev = m->rprev;
+    io->dots = m->dots;
+    io->dots_h = m->dots_h;
+    io->apply = mg_apply_fcg;
+    return TO3D_OK;
+}
+
+// ------------------------------------------------------------------ training
+// Loss of the current parameters over the snapshots (mean energy-norm error
+// of one application, FP64 operator and dots).
+static to3d_status snapshot_loss(to3d_ctx* c, double* loss) {
+    Mg* m = mg_of(c);
+    cudaStream_t s = c->stream;
+    const long long ndof = 3 * c->g.nnode;
+    m->params_dirty = true;
+    to3d_status st = ready(c);
+    if (st) return st;
+    double sum = 0.0;
+    for (auto& sn : m->snaps) {
+        if ((st = mg_apply64(c, sn.r, m->z64, sn.rn))) return st;
+        // z is 0 on clamped dofs, where the FP64 operator has identity rows
+        launch_matvec64(c, s, c->E, m->z64, c->tmp, false);
+        launch_dots64(c, s, ndof, m->z64, c->tmp, m->z64, sn.r, m->dots);
+        MG_CK(cudaMemcpyAsync(m->dots_h, m->dots, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+        MG_CK(cudaStreamSynchronize(s));
+        const double zkz = m->dots_h[0], zr = m->dots_h[1];
+        sum += (zkz - 2.0 * zr + sn.rte) / sn.rte;
+    }
+    *loss = m->snaps.empty() ? 0.0 : sum / (double)m->snaps.size();
+    if (!std::isfinite(*loss)) *loss = 1e30;
+    return TO3D_OK;
+}
+
+static unsigned long long splitmix(unsigned long long& x) {
+    unsigned long long z = (x += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// Parameters <-> unconstrained coordinates: w = 0.05 + 0.9 sigmoid(a),
+// q = exp(b) in [0.125, 8], s = exp(c) in (0, 64].
+static void to_free(const double* th, double* u) {
+    for (int g = 0; g < kGroups; ++g) {
+        const double y = (th[g] - 0.05) / 0.9;
+        u[g] = std::log(y / (1.0 - y));
+    }
+    for (int i = kGroups; i < kParams; ++i) u[i] = std::log(th[i]);
+}
+static void from_free(const double* u, double* th) {
+    for (int g = 0; g < kGroups; ++g) th[g] = 0.05 + 0.9 / (1.0 + std::exp(-u[g]));
+    for (int i = kGroups; i < 2 * kGroups - 1; ++i) th[i] = std::fmin(8.0, std::fmax(0.125, std::exp(u[i])));
+    for (int i = 2 * kGroups - 1; i < kParams; ++i) th[i] = std::fmin(64.0, std::exp(u[i]));
+}
+
+}  // namespace to3d
+
+using namespace to3d;
+
+extern "C" {
+
+to3d_status to3d_mg_param_count(to3d_ctx* c, int64_t* n) {
+    if (!c || !n) return TO3D_EINVAL;
+    *n = kParams;
+    return TO3D_OK;
+}
+
+to3d_status to3d_mg_get_params(to3d_ctx* c, double* theta, int64_t n) {
+    if (!c || !theta || n != kParams) return TO3D_EINVAL;
+    to3d_status st = ensure_mg(c);
+    if (st) return st;
+    std::memcpy(theta, mg_of(c)->theta, sizeof(double) * kParams);
+    return TO3D_OK;
+}
+
+to3d_status to3d_mg_set_params(to3d_ctx* c, const double* theta, int64_t n) {
+    if (!c || !theta || n != kParams) return TO3D_EINVAL;
+    if (!theta_valid(theta)) return set_err(c, TO3D_EINVAL, "multigrid parameters out of range");
+    to3d_status st = ensure_mg(c);
+    if (st) return st;
+    Mg* m = mg_of(c);
+    std::memcpy(m->theta, theta, sizeof(double) * kParams);
+    m->params_dirty = true;
+    m->trained = true;
+    return TO3D_OK;
+}
+
+to3d_status to3d_mg_levels(to3d_ctx* c, int32_t* nlev) {
+    if (!c || !nlev) return TO3D_EINVAL;
+    to3d_status st = ensure_mg(c);
+    if (st) return st;
+    *nlev = (int32_t)mg_of(c)->lv.size();
+    return TO3D_OK;
+}
+
+to3d_status to3d_mg_apply(to3d_ctx* c, const double* x, const double* r, double* z, int32_t on_device) {
+    if (!c || !x || !r || !z) return TO3D_EINVAL;
+    const long long ndof = 3 * c->g.nnode;
+    const void *dx = nullptr, *dr = nullptr;
+    to3d_status st;
+    if ((st = stage_input(c, x, sizeof(double) * c->g.nel, on_device, 0, &dx))) return st;
+    if ((st = stage_input(c, r, sizeof(double) * ndof, on_device, 1, &dr))) return st;
+    if ((st = prepare_op(c, (const double*)dx))) return st;
+    if ((st = ensure_mg(c))) return st;
+    mg_of(c)->params_dirty = true;
+    launch_norm2(c, c->stream, (const double*)dr, ndof, c->misc + 4);
+    double rr = 0.0;
+    MG_CK(cudaMemcpyAsync(&rr, c->misc + 4, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    MG_CK(cudaStreamSynchronize(c->stream));
+    double* dz = on_device ? z : c->tmp;
+    if ((st = mg_apply64(c, (const double*)dr, dz, std::sqrt(rr)))) return st;
+    if (!on_device) MG_CK(cudaMemcpyAsync(z, dz, sizeof(double) * ndof, cudaMemcpyDeviceToHost, c->stream));
+    MG_CK(cudaStreamSynchronize(c->stream));
+    return launch_check(c, "mg apply");
+}
+
+// Snapshots from the context's current design: residuals of FP64 Jacobi-PCG
+// from u = 0 after a random number (0..maxk) of iterations, with r^T K^-1 r
+// from an FP64 solve of K e = r to 1e-10; then `steps` Adam steps on
+// central-difference gradients of the mean loss.
+to3d_status to3d_mg_train(to3d_ctx* c, int32_t nsnap, int32_t steps, double lr, uint64_t seed,
+                          double* loss_first, double* loss_last) {
+    if (!c || nsnap < 1 || nsnap > 256 || steps < 0 || !(lr > 0) || !loss_first || !loss_last)
+        return TO3D_EINVAL;
+    to3d_status st = ensure_mg(c);
+    if (st) return st;
+    Mg* m = mg_of(c);
+    cudaStream_t s = c->stream;
+    const long long ndof = 3 * c->g.nnode;
+    if ((st = prepare_op(c, c->x))) return st;
+    for (auto& sn : m->snaps) cudaFree(sn.r);
+    m->snaps.clear();
+    unsigned long long rng = seed * 0x2545F4914F6CDD1DULL + 12345u;
+    for (int i = 0; i < nsnap; ++i) {
+        const int k = (int)(splitmix(rng) % 201ULL);
+        Snap sn;
+        MG_CK(cudaMalloc(&sn.r, sizeof(double) * ndof));
+        m->snaps.push_back(sn);
+        if ((st = run_pcg64_iters(c, c->f, k))) return st;
+        MG_CK(cudaMemcpyAsync(m->snaps.back().r, c->r, sizeof(double) * ndof, cudaMemcpyDeviceToDevice, s));
+        launch_norm2(c, s, m->snaps.back().r, ndof, c->misc + 4);
+        double rr = 0.0;
+        MG_CK(cudaMemcpyAsync(&rr, c->misc + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
+        MG_CK(cudaStreamSynchronize(s));
+        m->snaps.back().rn = std::sqrt(rr);
+        to3d_solve_info si{};
+        if ((st = solve64_rtol(c, m->snaps.back().r, std::sqrt(rr), 1e-10, &si))) return st;
+        launch_dots64(c, s, ndof, m->snaps.back().r, c->u, nullptr, nullptr, m->dots);
+        MG_CK(cudaMemcpyAsync(m->dots_h, m->dots, sizeof(double), cudaMemcpyDeviceToHost, s));
+        MG_CK(cudaStreamSynchronize(s));
+        m->snaps.back().rte = m->dots_h[0];
+        if (!(m->snaps.back().rte > 0.0)) return set_err(c, TO3D_ENUMERIC, "snapshot r^T K^-1 r <= 0");
+    }
+    c->have_u = false;
+    double u[kParams], mo[kParams] = {}, ve[kParams] = {}, gr[kParams], th[kParams];
+    to_free(m->theta, u);
+    double loss = 0.0;
+    if ((st = snapshot_loss(c, &loss))) return st;
+    *loss_first = loss;
+    double best = loss;
+    double best_th[kParams];
+    std::memcpy(best_th, m->theta, sizeof(best_th));
+    const double h = 0.05, b1 = 0.9, b2 = 0.999;
+    for (int t = 1; t <= steps; ++t) {
+        for (int i = 0; i < kParams; ++i) {
+            double up[kParams], lp = 0.0, lm = 0.0;
+            std::memcpy(up, u, sizeof(up));
+            up[i] = u[i] + h;
+            from_free(up, m->theta);
+            if ((st = snapshot_loss(c, &lp))) return st;
+            up[i] = u[i] - h;
+            from_free(up, m->theta);
+            if ((st = snapshot_loss(c, &lm))) return st;
+            gr[i] = (std::fmin(lp, 1e3) - std::fmin(lm, 1e3)) / (2.0 * h);
+        }
+        for (int i = 0; i < kParams; ++i) {
+            mo[i] = b1 * mo[i] + (1 - b1) * gr[i];
+            ve[i] = b2 * ve[i] + (1 - b2) * gr[i] * gr[i];
+            const double mh = mo[i] / (1 - std::pow(b1, t)), vh = ve[i] / (1 - std::pow(b2, t));
+            u[i] -= lr * mh / (std::sqrt(vh) + 1e-12);
+        }
+        from_free(u, th);
+        std::memcpy(m->theta, th, sizeof(th));
+        if ((st = snapshot_loss(c, &loss))) return st;
+        if (c->trace) std::fprintf(stderr, "to3d: mg train step %d loss %.5f\n", t, loss);
+        if (loss < best) {
+            best = loss;
+            std::memcpy(best_th, th, sizeof(best_th));
+        }
+    }
+    std::memcpy(m->theta, best_th, sizeof(best_th));
+    m->params_dirty = true;
+    m->trained = true;
+    *loss_last = best;
+    return launch_check(c, "mg train");
+}
+
+}  // extern "C"

@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(256)
     k_pcg32_update(long long vol, float* __restrict__ d32, float* __restrict__ r32,
                    const float* __restrict__ p, const float* __restrict__ q,
                    const float* __restrict__ dinv, const uint8_t* __restrict__ maskp,
-                   const Reducer red, SolverScalars* ss) {
+                   const Reducer red, SolverScalars* ss, int jacobi_beta) {
     if (ss->done) return;
     __shared__ double sh[64];
     __shared__ double out[2];
@@ -234,12 +234,14 @@ __global__ void __launch_bounds__(256)
     double v[2] = {rzd, rrd};
     if (grid_sum<2>(red, v, sh, out) && threadIdx.x == 0) {
         const double rzn = out[0];
-        ss->beta = rzn / ss->rz;
-        ss->zcoef = 1.0;
-        ss->rz = rzn;
+        if (jacobi_beta) {
+            ss->beta = rzn / ss->rz;
+            ss->zcoef = 1.0;
+            ss->rz = rzn;
+        }
         ss->rr = out[1];
         ss->it += 1;
-        if (!isfinite(rzn) || !isfinite(out[1])) {
+        if ((jacobi_beta && !isfinite(rzn)) || !isfinite(out[1])) {
             ss->status = TO3D_ENUMERIC;
             ss->done = 1;
         } else if (out[1] <= ss->tol2) {
@@ -248,6 +250,24 @@ __global__ void __launch_bounds__(256)
             ss->status = TO3D_ENOCONV;
             ss->done = 1;
         }
+    }
+}
+
+// out[0] = a.b, out[1] = cc.d (cc may be null)
+__global__ void k_dots64(long long n, const double* __restrict__ a, const double* __restrict__ b,
+                         const double* __restrict__ cc, const double* __restrict__ d,
+                         const Reducer red, double* out_dev) {
+    __shared__ double sh[64];
+    __shared__ double o2[2];
+    double s0 = 0.0, s1 = 0.0;
+    for (long long i = gtid(); i < n; i += gstride()) {
+        s0 = fma(a[i], b[i], s0);
+        if (cc) s1 = fma(cc[i], d[i], s1);
+    }
+    double v[2] = {s0, s1};
+    if (grid_sum<2>(red, v, sh, o2) && threadIdx.x == 0) {
+        out_dev[0] = o2[0];
+        out_dev[1] = o2[1];
     }
 }
 
@@ -361,9 +381,21 @@ void launch_pcg32_iter(to3d_ctx* c, cudaStream_t s, int prec, int parity, cudaEv
     if (ev0) cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal);
     launch_matvec_tc(c, s, prec, true, parity);
     if (ev1) cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal);
+    launch_pcg32_update_mode(c, s, p_new, 1);
+}
+
+// d += alpha p_new, r -= alpha q, |r|^2; with jacobi_beta also r.M^-1 r and
+// beta = rz_new / rz (Jacobi PCG); without, the caller forms beta itself.
+void launch_pcg32_update_mode(to3d_ctx* c, cudaStream_t s, const float* p_new, int jacobi_beta) {
     k_pcg32_update<<<vec_blocks(c->vol / 4), PCG_THREADS, 0, s>>>(c->vol, c->d32, c->r32, p_new,
                                                               c->q32, c->dinv32, c->maskp, c->red,
-                                                              c->ss);
+                                                              c->ss, jacobi_beta);
+    c->launches++;
+}
+
+void launch_dots64(to3d_ctx* c, cudaStream_t s, long long n, const double* a, const double* b,
+                   const double* cc, const double* d, double* out_dev) {
+    k_dots64<<<vec_blocks(n), PCG_THREADS, 0, s>>>(n, a, b, cc, d, c->red, out_dev);
     c->launches++;
 }
 

@@ -51,7 +51,7 @@ def test_default_params(lib):
     ("nelx", 0), ("nely", -1), ("volfrac", 0.0), ("volfrac", 1.5), ("penal", 0.5),
     ("rmin", 0.0), ("E0", 0.0), ("Emin", 0.0), ("Emin", 2.0), ("nu", 0.5), ("nu", -1.0),
     ("move", 0.0), ("bisect_tol", 0.0), ("cg_rtol", 0.0), ("cg_maxit", 0), ("oc_levels", 0),
-    ("oc_levels", 6), ("precision", 5), ("precision", -1), ("precond", 2), ("filter", 2),
+    ("oc_levels", 6), ("precision", 5), ("precision", -1), ("precond", 3), ("filter", 2),
     ("fcg_ref_iters", -1)])
 def test_create_rejects_bad_parameters(lib, field, value):
     assert create(lib, params(lib, **{field: value})) == 1       # TO3D_EINVAL
