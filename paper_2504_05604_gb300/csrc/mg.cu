@@ -553,8 +553,12 @@ static void mgpcg_iter(to3d_ctx* c, Mg* m, cudaStream_t s, int prec, int parity)
     launch_pcg32_update_mode(c, s, p_new, 0);
 }
 
+// Inner iterations per captured chunk (even, so the direction ping-pong stays
+// in phase across chunks).
+constexpr int kMgChunk = 8;
+
 static to3d_status mgpcg_chunk(to3d_ctx* c, Mg* m, int prec, int n) {
-    if (n == c->chunk) {
+    if (n == kMgChunk) {
         if (!m->pcg || m->pcg_prec != prec) {
             if (m->pcg) cudaGraphExecDestroy(m->pcg);
             m->pcg = nullptr;
@@ -602,16 +606,11 @@ to3d_status solve_dc_mg(to3d_ctx* c, const double* f, double fnorm, to3d_solve_i
         k_pcg_init<<<nblocks(c->g.nnode), kThreads, 0, c->stream>>>(
             c->g, c->px, c->vol, c->r, scale, c->nodemask, c->r32, c->d32, c->p32b, c->q32, c->red, c->ss);
         c->launches++;
-        int n = 4, it0 = 0;
         for (;;) {
-            const int chunk_n = n < c->chunk ? n : c->chunk;
-            if ((st = mgpcg_chunk(c, m, prec, chunk_n))) return st;
+            if ((st = mgpcg_chunk(c, m, prec, kMgChunk))) return st;
             if ((st = sync_solver_scalars(c))) return st;
-            it0 = c->ss_h->it;
             if (c->ss_h->done) break;
-            if (n < c->chunk) n *= 2;
         }
-        (void)it0;
         const int its = c->ss_h->it;
         total += its;
         if (c->ss_h->status == TO3D_ETIMEOUT || c->ss_h->status == TO3D_ENUMERIC) {
