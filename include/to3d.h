@@ -327,9 +327,12 @@ TO3D_API to3d_status to3d_conv3d_backward(int32_t Z, int32_t Y, int32_t X, int32
  *              the unit KE (s = 2 gives the Galerkin operator for a uniform
  *              modulus);
  *   transfer   trilinear prolongation P, restriction P^T, clamped dofs 0;
- *   smoother   damped Jacobi with weight w_l, one sweep before and one after
- *              the coarse correction; params.mg_sweeps sweeps (default 16)
- *              on the coarsest level.
+ *   smoother   damped Jacobi, one sweep before and one after the coarse
+ *              correction, params.mg_sweeps sweeps (default 16) on the
+ *              coarsest level; damping w_l * 2 / lam_l, lam_l = min(1.2 rq,
+ *              l1) with rq the Rayleigh quotient of D^-1 K after 16 power
+ *              steps from a fixed hashed start and l1 = max_a sum_b
+ *              |KE_ab| / KE_aa, so every sweep converges for 0 < w < 1.
  * The cycle runs in FP32 with the tensor-core operator (the context's
  * operand form; BF16 for TO3D_F64) on every level.  With TO3D_F64 it
  * preconditions FP64 flexible CG (the Jacobi-PCG fallback as for
@@ -338,7 +341,7 @@ TO3D_API to3d_status to3d_conv3d_backward(int32_t Z, int32_t Y, int32_t X, int32
  * params.inner_rtol).
  * Parameters theta (10 doubles, to3d_mg_param_count): w_0, w_1, w_2, w_3,
  * q_1, q_2, q_3, s_1, s_2, s_3, where index g applies to level min(l, 3), so
- * parameters learned on one grid size apply to any other.  Defaults: w = 0.5,
+ * parameters learned on one grid size apply to any other.  Defaults: w = 2/3,
  * q = 1, s = 2.  Valid ranges: 0 < w < 1, 1/8 <= q <= 8, 0 < s <= 64
  * (TO3D_EINVAL otherwise).  The first call that needs the hierarchy creates
  * one coarse context per level (device allocations). */

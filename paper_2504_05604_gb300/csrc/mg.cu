@@ -15,9 +15,13 @@
 //               child slots of E^q_l)^(1/q_l), missing children 0 (s = 2 and
 //               any q give the Galerkin operator for a uniform modulus).
 //   transfer    trilinear prolongation, restriction its transpose.
-//   smoother    damped Jacobi with weight w_l, one sweep before and one
-//               after the coarse correction; `sweeps` sweeps on the coarsest
-//               level.
+//   smoother    damped Jacobi, one sweep before and one after the coarse
+//               correction, `sweeps` sweeps on the coarsest level; damping
+//               om_l = w_l * 2 / lam_l with lam_l = min(1.2 rq_l, l1), rq_l
+//               the Rayleigh quotient of D^-1 K after 16 power steps from a
+//               fixed hashed start vector, l1 = max_a sum_b |KE_ab| / KE_aa
+//               (no modulus field exceeds it): every sweep with 0 < w < 1
+//               converges, also on nodes bounded by void elements.
 //   learned     theta = (w_g for g = 0..3, q_g and s_g for g = 1..3), group g
 //               = min(level, 3), so parameters learned on one grid size apply
 //               to any other.  Training minimises the energy-norm error that
@@ -70,7 +74,9 @@ struct Snap {
 struct Mg {
     std::vector<Level> lv;
     double theta[kParams];
-    float* wdev = nullptr;            // smoothing weight per level (device)
+    float* wdev = nullptr;            // damping per level (device)
+    double* lamdev = nullptr;         // eigenvalue bound per level (device)
+    double l1 = 59.0 / 11.0;          // max_a sum_b |KE_ab| / KE_aa
     int sweeps = 16;
     int prec = TO3D_BF16_DC;
     cudaGraphExec_t cycle = nullptr;  // ctx->r32 -> lv[0].z, captured
@@ -93,8 +99,11 @@ static double w_of(const Mg* m, int l) { return m->theta[group(l)]; }
 static double q_of(const Mg* m, int l) { return m->theta[kGroups + group(l) - 1]; }
 static double s_of(const Mg* m, int l) { return m->theta[2 * kGroups - 1 + group(l) - 1]; }
 
+constexpr int kPowerSteps = 16;
+constexpr double kPowerMargin = 1.2;
+
 static void default_theta(double* th) {
-    for (int g = 0; g < kGroups; ++g) th[g] = 0.5;
+    for (int g = 0; g < kGroups; ++g) th[g] = 2.0 / 3.0;
     for (int g = 1; g < kGroups; ++g) {
         th[kGroups + g - 1] = 1.0;
         th[2 * kGroups - 1 + g - 1] = 2.0;
@@ -103,7 +112,7 @@ static void default_theta(double* th) {
 
 static bool theta_valid(const double* th) {
     for (int g = 0; g < kGroups; ++g)
-        if (!(th[g] > 0.0 && th[g] < 1.0)) return false;
+        if (!(th[g] > 0.0 && th[g] < 1.0)) return false;   // fraction of the stability limit
     for (int g = 1; g < kGroups; ++g) {
         const double q = th[kGroups + g - 1], s = th[2 * kGroups - 1 + g - 1];
         if (!(q >= 0.125 && q <= 8.0) || !(s > 0.0 && s <= 64.0)) return false;
@@ -331,6 +340,78 @@ __global__ void k_pcg_init(const Grid g, int px, long long vol, const double* __
     }
 }
 
+// Power iteration for lam_max(D^-1 K).  Start: entry of dof d = 3 node + c
+// is frac(d * 2654435761 / 2^32) - 1/2 (Knuth's multiplicative hash), 0 on
+// clamped dofs, nodes with D = 0 and pads.
+__global__ void k_pow_start(const Grid g, int px, long long vol, const float* __restrict__ dinv,
+                            const uint8_t* __restrict__ maskp, float* __restrict__ z) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < vol;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(p % px);
+        const long long jk = p / px;
+        const long long node = i + (long long)g.nx * jk;
+        const uint8_t m = maskp[p];
+        const bool ok = i < g.nx && dinv[p] > 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const uint32_t h = (uint32_t)(3 * node + c) * 2654435761u;
+            z[c * vol + p] = (ok && !((m >> c) & 1)) ? (float)((double)h * 0x1p-32 - 0.5) : 0.f;
+        }
+    }
+}
+
+// out[0] = z.t, out[1] = z.D z (D = 1 / dinv on dofs with dinv > 0)
+__global__ void k_pow_dots(long long vol, const float* __restrict__ z, const float* __restrict__ t,
+                           const float* __restrict__ dinv, const uint8_t* __restrict__ maskp,
+                           const Reducer red, double* out_dev) {
+    __shared__ double sh[64];
+    __shared__ double o2[2];
+    double a = 0.0, b = 0.0;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < vol;
+         n += (long long)gridDim.x * blockDim.x) {
+        const float di = dinv[n];
+        const uint8_t m = maskp[n];
+        if (!(di > 0.f)) continue;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if ((m >> c) & 1) continue;
+            const double zv = z[c * vol + n];
+            a = fma(zv, (double)t[c * vol + n], a);
+            b = fma(zv, zv / (double)di, b);
+        }
+    }
+    double v[2] = {a, b};
+    if (grid_sum<2>(red, v, sh, o2) && threadIdx.x == 0) {
+        out_dev[0] = o2[0];
+        out_dev[1] = o2[1];
+    }
+}
+
+// z = D^-1 t / rq, rq = out[0] / out[1]
+__global__ void k_pow_next(long long vol, const float* __restrict__ t, const float* __restrict__ dinv,
+                           const uint8_t* __restrict__ maskp, const double* __restrict__ out,
+                           float* __restrict__ z) {
+    const double rq = out[1] > 0.0 ? out[0] / out[1] : 1.0;
+    const float inv = (float)(rq > 0.0 ? 1.0 / rq : 1.0);
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < vol;
+         n += (long long)gridDim.x * blockDim.x) {
+        const float di = dinv[n] * inv;
+        const uint8_t m = maskp[n];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) z[c * vol + n] = ((m >> c) & 1) ? 0.f : di * t[c * vol + n];
+    }
+}
+
+// wdev[l] = w * 2 / min(margin rq, l1)
+__global__ void k_pow_final(const double* __restrict__ out, double w, double margin, double l1,
+                            float* __restrict__ wdev, int l, double* __restrict__ lam_out) {
+    const double rq = out[1] > 0.0 ? out[0] / out[1] : l1;
+    const double lam = fmin(margin * rq, l1);
+    const double lam_ok = lam > 0.0 ? lam : l1;
+    wdev[l] = (float)(w * 2.0 / lam_ok);
+    lam_out[l] = lam_ok;
+}
+
 static unsigned nblocks(long long n) {
     long long b = (n + kThreads - 1) / kThreads;
     if (b > 152 * 8) b = 152 * 8;
@@ -354,7 +435,7 @@ void destroy_mg(to3d_ctx* c) {
         if (l > 0) to3d_destroy(m->lv[l].ctx);
     }
     for (auto& s : m->snaps) cudaFree(s.r);
-    void* ptrs[] = {m->wdev, m->z64, m->rprev, m->dots, m->ones};
+    void* ptrs[] = {m->wdev, m->lamdev, m->z64, m->rprev, m->dots, m->ones};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (m->dots_h) cudaFreeHost(m->dots_h);
@@ -423,6 +504,16 @@ static to3d_status ensure_mg(to3d_ctx* c) {
     }
     const long long ndof = 3 * g0.nnode;
     MG_CK(cudaMalloc(&m->wdev, sizeof(float) * kMaxLevels));
+    MG_CK(cudaMalloc(&m->lamdev, sizeof(double) * kMaxLevels));
+    {
+        double l1 = 0.0;
+        for (int a = 0; a < 24; ++a) {
+            double row = 0.0;
+            for (int b = 0; b < 24; ++b) row += std::fabs(c->ke.v[a * 24 + b]);
+            l1 = std::fmax(l1, row / c->ke.v[a * 24 + a]);
+        }
+        m->l1 = l1;
+    }
     MG_CK(cudaMalloc(&m->z64, sizeof(double) * ndof));
     MG_CK(cudaMalloc(&m->rprev, sizeof(double) * ndof));
     MG_CK(cudaMalloc(&m->dots, sizeof(double) * 4));
@@ -440,9 +531,6 @@ static to3d_status ensure_mg(to3d_ctx* c) {
 static to3d_status setup_levels(to3d_ctx* c) {
     Mg* m = mg_of(c);
     cudaStream_t s = c->stream;
-    float w[kMaxLevels];
-    for (int l = 0; l < kMaxLevels; ++l) w[l] = (float)w_of(m, l);
-    MG_CK(cudaMemcpyAsync(m->wdev, w, sizeof(w), cudaMemcpyHostToDevice, s));
     for (size_t l = 1; l < m->lv.size(); ++l) {
         to3d_ctx* f = m->lv[l - 1].ctx;
         to3d_ctx* k = m->lv[l].ctx;
@@ -450,6 +538,21 @@ static to3d_status setup_levels(to3d_ctx* c) {
             f->g, f->E, k->g, q_of(m, (int)l), s_of(m, (int)l), k->E, k->E32, k->pex);
         launch_diag(k, s, k->E);
         c->launches += 2;
+    }
+    // damping of every level from its eigenvalue bound
+    for (size_t l = 0; l < m->lv.size(); ++l) {
+        Level& L = m->lv[l];
+        to3d_ctx* k = L.ctx;
+        double* out = k->misc + 4;
+        k_pow_start<<<nblocks(k->vol), kThreads, 0, s>>>(k->g, k->px, k->vol, k->dinv32, k->maskp, L.z);
+        for (int it = 0; it < kPowerSteps; ++it) {
+            launch_matvec_tc_io(k, s, m->prec, false, k->tm_r, L.tm_z, k->tm_d, nullptr, L.t, nullptr);
+            k_pow_dots<<<nblocks(k->vol), kThreads, 0, s>>>(k->vol, L.z, L.t, k->dinv32, k->maskp, k->red, out);
+            if (it + 1 < kPowerSteps)
+                k_pow_next<<<nblocks(k->vol), kThreads, 0, s>>>(k->vol, L.t, k->dinv32, k->maskp, out, L.z);
+        }
+        k_pow_final<<<1, 1, 0, s>>>(out, w_of(m, (int)l), kPowerMargin, m->l1, m->wdev, (int)l, m->lamdev);
+        c->launches += 2 + 3 * kPowerSteps;
     }
     m->params_dirty = false;
     return launch_check(c, "multigrid set-up");

@@ -44,7 +44,7 @@ def test_cycle_matches_oracle(dims, prec, tol):
     r = problems.random_vector(prob.ndof, 4)
     ctx = lib_ctx(prob, precision=prec, precond=LMG)
     theta = ctx.mg_params()
-    assert np.allclose(theta, [0.5] * 4 + [1.0] * 3 + [2.0] * 3)
+    assert np.allclose(theta, [2.0 / 3.0] * 4 + [1.0] * 3 + [2.0] * 3)
     z = ctx.mg_apply(x, r)
     zr, nlev = oracle_cycle(prob, x, r, theta)
     assert ctx.mg_levels() == nlev

@@ -101,7 +101,7 @@ def test_one_level_vcycle_is_damped_jacobi():
     mg.setup(lv, E, KE, [1.0], [1.0])
     free = ~lv[0].fixed
     K = fem.assemble(4, 3, 2, E, KE).toarray() * np.outer(free, free)
-    Dw = np.diag(0.45 * lv[0].dinv)
+    Dw = np.diag(mg.damping(lv[0], 0.45) * lv[0].dinv)
     T = np.eye(K.shape[0]) - Dw @ K
     V = sum(np.linalg.matrix_power(T, k) for k in range(7)) @ Dw
     b = np.where(lv[0].fixed, 0, np.random.default_rng(1).standard_normal(K.shape[0]))
@@ -153,3 +153,25 @@ def test_vcycle_preconditioner_beats_jacobi_on_a_cantilever():
     it_j = pcg(lambda r: r / d)
     it_mg = pcg(lambda r: mg.vcycle(lv, KE, r, w, 20))
     assert it_mg * 3 < it_j, (it_mg, it_j)
+
+
+def test_eigenvalue_estimate_bounds_the_smoother():
+    """The eigenvalue bound the smoother uses is at least the exact
+    lam_max(D^-1 K) (so the damping 2 w / lam keeps every sweep convergent)
+    and not far above it, on a graded design with void elements next to
+    solid ones; the l1 bound holds for any moduli."""
+    prob = problems.cantilever(6, 4, 4, load="edge")
+    x = problems.random_density(prob.nel, 12, 0.0, 1.0)
+    x[::3] = 0.0
+    E = fem.simp_modulus(x, 3.0)
+    KE = fem.element_stiffness(0.3)
+    lv = mg.hierarchy(6, 4, 4, prob.fixed)
+    mg.setup(lv, E, KE, [1.0] * len(lv), [1.0] * len(lv))
+    L = lv[0]
+    free = ~L.fixed
+    K = fem.assemble(6, 4, 4, E, KE).toarray()[np.ix_(free, free)]
+    d = np.diag(K)
+    lam = np.linalg.eigvalsh(K / np.sqrt(np.outer(d, d)))[-1]
+    assert lam <= L.lam <= 1.2 * lam
+    assert 0.85 * lam <= mg.rayleigh_power(L, KE) <= lam * (1 + 1e-12)
+    assert lam <= mg.l1_bound(KE) and mg.l1_bound(KE) == pytest.approx(59.0 / 11.0, rel=1e-12)
