@@ -1,12 +1,20 @@
 #!/usr/bin/env python3
 """OC iterations per second of the SIMP + OC hot path on a 480x160x80 cantilever.
 
-One step = one OC iteration of the whole path (SIMP moduli and Jacobi
-diagonal, equilibrium solve to ||f - K u|| <= 1e-8 ||f||, element energies and
+One step = one OC iteration of the whole path (SIMP moduli, preconditioner
+set-up, equilibrium solve to ||f - K u|| <= 1e-8 ||f||, element energies and
 sensitivities, rmin filter, OC bisection update) on the synthetic cantilever
 480x160x80 (load at the centre of the x = nelx face, volfrac 0.2, rmin 2.5).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P]
+The chosen form: BF16 tensor-core operator with FP32 inner CG and FP64
+defect correction, preconditioned by the learned multigrid V-cycle (its
+parameters learned first on a 96x32x16 cantilever of the same family).
+Beside it, on the same three designs of the timed window (its start, middle
+and end, each with the displacement the run had there): plain FP64
+Jacobi-PCG, the learned-FCG form (FP64 flexible CG with the learned
+multigrid) and the Jacobi-preconditioned defect correction.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P] [--precond lmg|jacobi]
   python bench.py --impl reference ...    (the CPU FP64 oracle, bounded sample)
 
 Prints one JSON line (rank 0).  N > 1 (torchrun): independent replicas, one
@@ -46,12 +54,15 @@ ARITHMETIC = {
 # at 480x160x80 needs 5116 iterations from the design after OC iteration 5
 # and 6321 from the one after iteration 10; about 5700 over iterations 4-11.
 REF_ITERS_PER_OC = 5700
+# the learned multigrid parameters are learned on this cantilever of the
+# bench's family (centre load, volfrac 0.2, rmin 2.5) after a few OC iterations
+TRAIN_GRID = (96, 32, 16)
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", type=int, default=1,
@@ -61,18 +72,24 @@ def parse():
     ap.add_argument("--workload", default="large", choices=["large", "batched64", "paper32"],
                     help="large: the 480x160x80 cantilever; batched64: 64 seeded uneven "
                          "cantilevers stepped together (extra measurement)")
-    ap.add_argument("--inner-rtol", type=float, default=0.3,
-                    help="residual-replacement factor of the defect-correction forms")
-    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison step")
+    ap.add_argument("--precond", default="lmg", choices=["lmg", "jacobi"],
+                    help="lmg: learned multigrid (the chosen form); jacobi: Jacobi-PCG")
+    ap.add_argument("--inner-rtol", type=float, default=None,
+                    help="residual-replacement factor of the defect-correction forms "
+                         "(default 0.01 with the multigrid, 0.3 with Jacobi)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the comparison forms")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--learned", action="store_true",
-                    help="also time one OC iteration of the learned-FCG form (network trained "
-                         "first on a 96x32x16 cantilever; several minutes)")
+    ap.add_argument("--unet", action="store_true",
+                    help="also time one OC iteration of the U-Net flexible-CG form (network "
+                         "trained first on a 96x32x16 cantilever; several minutes)")
     ap.add_argument("--cpu-leg", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-its", type=float, default=REF_ITERS_PER_OC, help=argparse.SUPPRESS)
-    ap.add_argument("--cpu-reps", type=int, default=1, help=argparse.SUPPRESS)
-    return ap.parse_args()
+    ap.add_argument("--cpu-reps", type=int, default=20, help=argparse.SUPPRESS)
+    a = ap.parse_args()
+    if a.inner_rtol is None:
+        a.inner_rtol = 0.01 if a.precond == "lmg" else 0.3
+    return a
 
 
 def dims(args):
@@ -133,59 +150,55 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle leg
 def cpu_leg(args):
-    """Time the CPU oracle on a bounded sample of the workload and
-    extrapolate to OC iterations/s (prints one JSON dict)."""
+    """Time the oracle's assembled-CSR FP64 Jacobi-PCG and element steps (C,
+    OpenMP, all host cores) on a slab of the workload and extrapolate to OC
+    iterations/s at the full grid (prints one JSON dict)."""
     import numpy as np
-    from oracle import fem, filters, oc
+    from oracle import csr, fem
     from synth import problems
 
     nelx, nely, nelz = dims(args)
     KE = fem.element_stiffness(0.3)
-    # Jacobi-PCG iteration cost on a quarter-depth slab of the grid (maxit=2
-    # minus maxit=1; each call also forms the initial and final residuals),
-    # scaled to the full grid by element count
-    zp = max(1, nelz // 4)
-    sp = problems.config_large(nelx=nelx, nely=nely, nelz=zp)
+    zs = max(1, nelz // 8)                  # an eighth-depth slab of the grid
+    sp = problems.config_large(nelx=nelx, nely=nely, nelz=zs)
     x = sp.initial_density()
     E = fem.simp_modulus(x, sp.penal)
     f = fem.masked_load(sp.load, sp.fixed)
-    diag = fem.jacobi_diagonal(nelx, nely, zp, E, KE, sp.fixed)
-
-    def mv(v):
-        return fem.matvec_elementwise(nelx, nely, zp, E, KE, v, sp.fixed)
-
-    t = []
-    for m in (1, 2):
-        t0 = time.perf_counter()
-        fem.jacobi_pcg(mv, diag, f, rtol=0.0, maxit=m, true_residual=False)
-        t.append(time.perf_counter() - t0)
-    t_it = max(t[1] - t[0], 1e-9) * (nelz / zp)
-    # once-per-OC-iteration steps on an eighth-depth slab, scaled likewise
-    sz = max(1, nelz // 8)
-    sub = problems.config_large(nelx=nelx, nely=nely, nelz=sz)
-    xs = sub.initial_density()
-    us = problems.random_vector(sub.ndof, 1, 1e-3)
     t0 = time.perf_counter()
-    ce = fem.element_energies(nelx, nely, sz, KE, us)
-    c, dc = fem.compliance_and_sensitivity(xs, ce, sub.penal)
-    dcf = filters.sensitivity_filter_stencil(nelx, nely, sz, sub.rmin, xs, dc)
-    oc.oc_update(xs, dcf, sub.volfrac, None, sub.move, sub.bisect_tol)
-    t_el = (time.perf_counter() - t0) * (nelz / sz)
-    t_oc = args.cpu_its * t_it + t_el
-    cores = 1
+    op = csr.Operator(nelx, nely, zs, E, KE, sp.fixed)
+    t_asm = (time.perf_counter() - t0) * (nelz / zs)
+    # PCG iterations: reps iterations minus one, so the set-up cancels
+    reps = max(args.cpu_reps, 2)
+    t = []
+    for m in (1, reps + 1):
+        t0 = time.perf_counter()
+        op.pcg(f, rtol=0.0, maxit=m)
+        t.append(time.perf_counter() - t0)
+    t_it = max(t[1] - t[0], 1e-9) / reps * (nelz / zs)
+    op.close()
+    u = problems.random_vector(sp.ndof, 1, 1e-3)
+    t0 = time.perf_counter()
+    c, ce, dc = csr.element_steps(nelx, nely, zs, KE, u, x, sp.penal)
+    dcf = csr.sensitivity_filter(nelx, nely, zs, sp.rmin, x, dc)
+    csr.oc_update(x, dcf, sp.volfrac, None, sp.move, sp.bisect_tol)
+    t_el = (time.perf_counter() - t0) * (nelz / zs)
+    t_oc = args.cpu_its * t_it + t_el + t_asm
+    cores = csr.threads()
     return {"value": 1.0 / t_oc, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": (f"oracle (NumPy/SciPy FP64, single-threaded BLAS) on {nelx}x{nely}x{nelz}: "
-                       f"one Jacobi-PCG iteration timed on a {nelx}x{nely}x{zp} slab and scaled by "
-                       f"element count ({t_it:.2f} s), energies+"
-                       f"filter+OC timed on a {nelx}x{nely}x{sz} slab and scaled by element count "
-                       f"({t_el:.2f} s); OC iteration = {args.cpu_its:.0f} PCG iterations + those"),
-            "t_pcg_iter_s": t_it, "t_elementwise_s": t_el, "pcg_iters_per_oc": args.cpu_its}
+            "sample": (f"oracle's C part (assembled CSR, FP64 Jacobi-PCG, OpenMP on {cores} threads) "
+                       f"on a {nelx}x{nely}x{zs} slab of the {nelx}x{nely}x{nelz} grid: {reps} PCG "
+                       f"iterations timed ({t_it:.3f} s each at full size), CSR assembly "
+                       f"({t_asm:.2f} s) and energies + filter + OC ({t_el:.2f} s), each scaled by "
+                       f"element count; OC iteration = {args.cpu_its:.0f} PCG iterations (the "
+                       f"library's FP64 Jacobi-PCG count on the same designs) + the rest"),
+            "t_pcg_iter_s": t_it, "t_assembly_s": t_asm, "t_elementwise_s": t_el,
+            "pcg_iters_per_oc": args.cpu_its, "nproc": os.cpu_count()}
 
 
 def run_cpu_leg_subprocess(args, its):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    env = dict(os.environ, OMP_NUM_THREADS=str(os.cpu_count() or 1))
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-leg", "--size", args.size,
-           "--cpu-its", str(its)]
+           "--cpu-its", str(its), "--cpu-reps", str(args.cpu_reps)]
     r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
     if r.returncode != 0:
         return {"error": r.stderr[-400:]}
@@ -208,6 +221,7 @@ def reference_arm(args):
     if rank != 0:
         return
     vals = []
+    r = None
     for i in range(args.warmup + args.steps):
         r = run_cpu_leg_subprocess(args, args.cpu_its)
         if "error" in r:
@@ -253,8 +267,8 @@ def job_value(world: int, steps: int, ms: float) -> float:
 
 def algorithmic_bytes_tc(nelx, nely, nelz):
     """Per launch of the fused tensor-core matvec + direction kernel:
-    read r, p_old (4 B/dof each), M^-1 (4 B/node), E (4 B/element); write
-    p_new and q (4 B/dof each)."""
+    read r (or z), p_old (4 B/dof each), the per-node scaling (4 B/node), E
+    (4 B/element); write p_new and q (4 B/dof each)."""
     N = (nelx + 1) * (nely + 1) * (nelz + 1)
     nel = nelx * nely * nelz
     n = 3 * N
@@ -281,12 +295,31 @@ def _peaks():
         return {}
 
 
-def learned_leg(args, prob, stream, x_start, fp64_iters):
-    """One OC iteration of the learned-FCG form from the design the main run
-    reached: the U-Net preconditioner (trained first, on the GPU, on residual
-    snapshots of a 96x32x16 cantilever of the same family; the network is
-    fully convolutional) inside FP64 flexible CG with the Jacobi-PCG
-    fallback, to the same 1e-8 relative residual."""
+def train_lmg(stream):
+    """Learn the multigrid parameters on a 96x32x16 cantilever of the bench's
+    family after 6 OC iterations; returns (theta, record)."""
+    import torch
+    from paper_2504_05604_gb300 import LMG, Context
+    from synth import problems
+    small = problems.config_large(nelx=TRAIN_GRID[0], nely=TRAIN_GRID[1], nelz=TRAIN_GRID[2])
+    t0 = time.perf_counter()
+    tctx = Context.from_problem(small, precision=0, precond=LMG, stream=stream.cuda_stream)
+    for _ in range(6):
+        tctx.step()
+    first, last = tctx.mg_train(nsnap=8, steps=20, lr=0.1, seed=3)
+    theta = tctx.mg_params()
+    tctx.close()
+    torch.cuda.synchronize()
+    return theta, {"grid": "x".join(map(str, TRAIN_GRID)), "after_oc_iterations": 6,
+                   "snapshots": 8, "adam_steps": 20, "loss_first": first, "loss_last": last,
+                   "theta": [round(float(v), 4) for v in theta],
+                   "seconds": time.perf_counter() - t0}
+
+
+def unet_leg(prob, stream, x_start, fp64_iters):
+    """One OC iteration of the U-Net flexible-CG form from a design (the
+    network trained first, on the GPU, on residual snapshots of a 96x32x16
+    cantilever of the same family)."""
     import torch
     from paper_2504_05604_gb300 import CNN_FCG, Context
     from synth import problems
@@ -302,27 +335,6 @@ def learned_leg(args, prob, stream, x_start, fp64_iters):
                                 fcg_ref_iters=int(fp64_iters))
     lctx.set_cnn_params(flat)
     lctx.set_density(x_start)
-    # one network application at full size (device buffers), CUDA events
-    xd = torch.as_tensor(x_start, device="cuda")
-    rd = torch.randn(prob.ndof, dtype=torch.float64, device="cuda")
-    zd = torch.empty_like(rd)
-    with torch.cuda.stream(stream):
-        lctx.cnn_apply(xd, rd, zd)
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for _ in range(3):
-            lctx.cnn_apply(xd, rd, zd)
-        a1.record(stream)
-    torch.cuda.synchronize()
-    apply_ms = a0.elapsed_time(a1) / 3
-    flops = cnn_flops(prob.nelx, prob.nely, prob.nelz)
-    peaks = _peaks()
-    bf16 = peaks.get("bf16_tflops", 1900.0)
-    cnn_apply = {"ms": apply_ms, "algorithmic_tflop": flops / 1e12,
-                 "achieved_tflops": flops / (apply_ms * 1e-3) / 1e12, "peak_tflops": bf16,
-                 "frac": flops / (apply_ms * 1e-3) / 1e12 / bf16, "bound": "tensor",
-                 "note": "whole U-Net incl. input/output and pooling kernels; convolutions on "
-                         "mma.sync BF16 tiles"}
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -334,8 +346,35 @@ def learned_leg(args, prob, stream, x_start, fp64_iters):
     return {"value": 1000.0 / ms, "unit": UNIT, "cg_iters": r["cg_iters"],
             "fell_back_to_jacobi_pcg": r["outer_iters"] == 2, "relres": r["relres"],
             "status": r["status"], "train_s": train_s, "train_loss_first": first,
-            "train_loss_last": last, "trained_on": "cantilever 96x32x16, 24 snapshots, 1500 Adam steps",
-            "cnn_apply": cnn_apply}
+            "train_loss_last": last}
+
+
+def form_on_designs(prob, stream, samples, **form):
+    """One OC iteration of a form from each sampled (design, displacement):
+    CUDA-event times, iterations and residuals."""
+    import torch
+    from paper_2504_05604_gb300 import Context
+    theta = form.pop("theta", None)
+    ctx = Context.from_problem(prob, stream=stream.cuda_stream, **form)
+    if theta is not None:
+        ctx.set_mg_params(theta)
+    out = []
+    for label, x, u in samples:
+        ctx.set_density(x)
+        ctx.set_displacement(u)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = ctx.step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out.append({"design": label, "value": 1000.0 / ms, "ms": ms, "cg_iters": r["cg_iters"],
+                    "outer_iters": r["outer_iters"], "relres": r["relres"],
+                    "status": r["status"], "compliance": r["compliance"]})
+    ctx.close()
+    return {"unit": UNIT, "value": len(out) / sum(o["ms"] / 1000.0 for o in out),
+            "per_design": out}
 
 
 def ours(args):
@@ -353,42 +392,70 @@ def ours(args):
 
     from paper_2504_05604_gb300 import build as libbuild
     libbuild.build()
-    from paper_2504_05604_gb300 import Context
+    from paper_2504_05604_gb300 import JACOBI, LMG, Context
     from synth import problems
 
     nelx, nely, nelz = dims(args)
     prob = problems.config_large(nelx=nelx, nely=nely, nelz=nelz)
     stream = torch.cuda.Stream(device=dev)
-    ctx = Context.from_problem(prob, precision=args.precision, stream=stream.cuda_stream,
-                               inner_rtol=args.inner_rtol)
+    lmg = args.precond == "lmg"
+    theta, train = (train_lmg(stream) if lmg else (None, None))
+    form = dict(precision=args.precision, precond=LMG if lmg else JACOBI,
+                inner_rtol=args.inner_rtol)
+
+    def make_ctx():
+        c = Context.from_problem(prob, stream=stream.cuda_stream, **form)
+        if theta is not None:
+            c.set_mg_params(theta)
+        return c
+
+    ctx = make_ctx()
     warm = [ctx.step() for _ in range(args.warmup)]
 
     def barrier():
         if world > 1:
             dist.barrier()
 
+    # the designs the comparison forms start from: the window's start,
+    # middle and end, each with the displacement the run had there (every
+    # form warm-starts from it); copied on the device, outside the timed parts
+    mid = args.steps // 2
+    xs = [torch.empty(prob.nel, dtype=torch.float64, device=dev) for _ in range(3)]
+    us = [torch.empty(prob.ndof, dtype=torch.float64, device=dev) for _ in range(3)]
+
+    def sample(i):
+        with torch.cuda.stream(stream):
+            ctx.density(xs[i])
+            ctx.displacement(us[i])
+
     with torch.cuda.stream(stream):
+        sample(0)
         ctx.kernel_stats(0, reset=True)
-        ctx.kernel_stats(1, reset=True)
         l0 = ctx.launches
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         clk = ClockSampler(local)
         barrier()
         torch.cuda.synchronize()
         clk.start()
-        ev0.record(stream)
-        recs = [ctx.step() for _ in range(args.steps)]
-        ev1.record(stream)
+        ev[0].record(stream)
+        recs = [ctx.step() for _ in range(mid)]
+        ev[1].record(stream)
+        sample(1)
+        ev[2].record(stream)
+        recs += [ctx.step() for _ in range(args.steps - mid)]
+        ev[3].record(stream)
         torch.cuda.synchronize()
         clocks = clk.stop()
         barrier()
-        ms = ev0.elapsed_time(ev1)
+        ms = ev[0].elapsed_time(ev[1]) + ev[2].elapsed_time(ev[3])
         launches = ctx.launches - l0
         tc_ms, tc_n = ctx.kernel_stats(0)
+        sample(2)
+        torch.cuda.synchronize()
     ms = max_over_ranks(ms, dev)
     value = job_value(world, args.steps, ms)
     status = max(r["status"] for r in recs)
-    its = [r["cg_iters"] + r["outer_iters"] for r in recs]
+    its = [r["cg_iters"] for r in recs]
 
     # end to end through the public API with host buffers, on the same OC
     # iterations: a second context repeats the warm-up, then every timed
@@ -396,8 +463,7 @@ def ours(args):
     # reads the new design and the iteration record back
     e2e = None
     if not args.no_e2e:
-        ctx_e = Context.from_problem(prob, precision=args.precision, stream=stream.cuda_stream,
-                                     inner_rtol=args.inner_rtol)
+        ctx_e = make_ctx()
         for _ in range(args.warmup):
             ctx_e.step()
         xh = torch.empty(prob.nel, dtype=torch.float64).pin_memory().numpy()
@@ -416,40 +482,22 @@ def ours(args):
                "h2d_bytes_per_step": 8 * prob.nel,
                "d2h_bytes_per_step": 8 * prob.nel + 112}
 
-    # plain FP64 Jacobi-PCG from the same design, one OC iteration
-    fp64 = None
-    if not args.no_fp64 and args.precision != 0:
-        ctx64 = Context.from_problem(prob, precision=0, stream=stream.cuda_stream)
-        xcur = ctx.density()
-        ctx64.set_density(xcur)
-        torch.cuda.synchronize()
-        ctx64.kernel_stats(1, reset=True)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        r64 = ctx64.step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        m64 = e0.elapsed_time(e1)
-        mv_ms, mv_n = ctx64.kernel_stats(1)
-        fp64 = {"value": 1000.0 / m64, "unit": UNIT, "cg_iters": r64["cg_iters"],
-                "relres": r64["relres"], "matvec_ms": mv_ms / max(mv_n, 1),
-                "oc_iter": r64["iter"], "from_design_after_iter": ctx.params.nelx and recs[-1]["iter"]}
-        ctx64.close()
-
-    learned = None
-    if args.learned:
-        learned = learned_leg(args, prob, stream, ctx.density(),
-                              fp64["cg_iters"] if fp64 else 0)
+    # the other forms, one OC iteration from each of the three designs
+    samples = [(f"after OC iteration {args.warmup + k}", xs[i], us[i])
+               for i, k in enumerate((0, mid, args.steps))]
+    fp64 = learned = jacobi_dc = None
+    if not args.no_fp64:
+        fp64 = form_on_designs(prob, stream, samples, precision=0)
+        learned = form_on_designs(prob, stream, samples, precision=0, precond=LMG, theta=theta)
+        jacobi_dc = form_on_designs(prob, stream, samples, precision=1, inner_rtol=0.3)
+    unet = None
+    if args.unet:
+        unet = unet_leg(prob, stream, xs[2].cpu().numpy(),
+                        fp64["per_design"][-1]["cg_iters"] if fp64 else 0)
 
     if rank != 0:
         return
-    import json as _json
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            peaks = _json.load(fh)
-    except OSError:
-        pass
+    peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     tc_avg_ms = tc_ms / tc_n if tc_n else None
     roof = None
@@ -457,22 +505,29 @@ def ours(args):
         b = algorithmic_bytes_tc(nelx, nely, nelz)
         ach = b / (tc_avg_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": TC_TRAFFIC_BYTES.get((args.precision, nelx, nely, nelz)), "kernel": "k_matvec_tc (fused direction + tensor-core K p)",
+                "traffic": TC_TRAFFIC_BYTES.get((args.precision, nelx, nely, nelz)),
+                "kernel": "k_matvec_tc (fused direction + tensor-core K p)",
                 "launch_ms": tc_avg_ms, "algorithmic_bytes": b, "samples": tc_n,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
     cpu = None
     if not args.no_cpu and world == 1:
         # the oracle solves with FP64 Jacobi-PCG: its iteration count is the
-        # plain FP64 form's, measured above when that leg ran
-        cpu = run_cpu_leg_subprocess(args, fp64["cg_iters"] if fp64 else REF_ITERS_PER_OC)
+        # plain FP64 form's on the same designs
+        n64 = (statistics.mean(o["cg_iters"] for o in fp64["per_design"]) if fp64
+               else REF_ITERS_PER_OC)
+        cpu = run_cpu_leg_subprocess(args, n64)
+    name = PREC_NAMES[args.precision] + ("-lmg" if lmg else "")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPES[args.precision],
         "data": "synthetic",
-        "config": dict(workload_config(args, world), form=PREC_NAMES[args.precision],
-                       arithmetic=ARITHMETIC[args.precision]),
+        "config": dict(workload_config(args, world), form=name,
+                       arithmetic=ARITHMETIC[args.precision] + (
+                           "; preconditioner: learned multigrid V-cycle (FP32, tensor-core "
+                           "operator on every level)" if lmg else "; Jacobi preconditioner"),
+                       inner_rtol=args.inner_rtol),
         "gpu_launches": int(launches),
         "status": int(status),
         "cg_iters_per_step": its,
@@ -481,11 +536,19 @@ def ours(args):
         "compliance": [r["compliance"] for r in recs],
         "clocks": clocks,
         "roofline": roof,
+        "lmg_training": train,
         "plain_fp64": fp64,
         "learned_fcg": learned,
+        "jacobi_dc": jacobi_dc,
+        "unet_fcg": unet,
         "e2e": e2e,
         "cpu_baseline": cpu,
     }
+    if fp64:
+        line["speedup_vs_plain_fp64_same_designs"] = {
+            "chosen_window": value / fp64["value"],
+            "learned_fcg": learned["value"] / fp64["value"],
+            "jacobi_dc": jacobi_dc["value"] / fp64["value"]}
     print(json.dumps(line))
     ctx.close()
     if world > 1:

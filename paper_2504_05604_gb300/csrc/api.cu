@@ -511,6 +511,7 @@ to3d_status true_residual64(to3d_ctx* c, const double* f, double fnorm, double* 
     return true_residual(c, f, fnorm, relres);
 }
 to3d_status sync_solver_scalars(to3d_ctx* c) { return sync_scalars(c); }
+void accumulate_tc_times(to3d_ctx* c, int it0, int it1) { accumulate_kernel_times(c, 0, it0, it1); }
 
 // FP64 Jacobi-PCG continuing from the current u (fallback of flexible CG)
 to3d_status solve64_from_u(to3d_ctx* c, const double* f, double fnorm, to3d_solve_info* info) {

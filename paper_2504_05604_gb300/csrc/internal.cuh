@@ -228,6 +228,9 @@ struct FcgIO {
 };
 to3d_status true_residual64(to3d_ctx* c, const double* f, double fnorm, double* relres);
 to3d_status sync_solver_scalars(to3d_ctx* c);
+// add the sampled tensor-core kernel durations of a completed chunk that
+// covered solver iterations [it0, it1)
+void accumulate_tc_times(to3d_ctx* c, int it0, int it1);
 void launch_pcg32_update_mode(to3d_ctx* c, cudaStream_t s, const float* p_new, int jacobi_beta);
 void launch_dots64(to3d_ctx* c, cudaStream_t s, long long n, const double* a, const double* b,
                    const double* cc, const double* d, double* out_dev);

@@ -164,9 +164,8 @@ __global__ void k_restrict(const Grid gf, int pxf, long long volf, const float* 
                            const Grid gc, int pxc, long long volc, const uint8_t* __restrict__ maskc,
                            float* __restrict__ bc, const SolverScalars* ss) {
     if (skip(ss)) return;
-    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (n >= gc.nnode) return;
-    const int i = n % gc.nx, j = (n / gc.nx) % gc.ny, k = n / ((long long)gc.nx * gc.ny);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= gc.nx) return;
     float acc[3] = {0.f, 0.f, 0.f};
     for (int dk = -1; dk <= 1; ++dk) {
         const int fk = 2 * k + dk;
@@ -199,9 +198,8 @@ __global__ void k_prolong(const Grid gf, int pxf, long long volf, const uint8_t*
                           float* __restrict__ zf, const Grid gc, int pxc, long long volc,
                           const float* __restrict__ zc, const SolverScalars* ss) {
     if (skip(ss)) return;
-    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (n >= gf.nnode) return;
-    const int i = n % gf.nx, j = (n / gf.nx) % gf.ny, k = n / ((long long)gf.nx * gf.ny);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= gf.nx) return;
     const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
     const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
     const float wi = (i & 1) ? 0.5f : 1.f, wj = (j & 1) ? 0.5f : 1.f, wk = (k & 1) ? 0.5f : 1.f;
@@ -280,12 +278,18 @@ __global__ void k_pcg_dots(long long vol, const float* __restrict__ r, const flo
     if (ss->done) return;
     __shared__ double sh[64];
     __shared__ double out[2];
+    // 3 vol is a multiple of 4: float4 loads; FP32 partial sums of 4 x 8
+    // products per thread and step, FP64 across steps, blocks and the grid
+    const long long n4 = (3 * vol) >> 2;
+    const float4* r4 = reinterpret_cast<const float4*>(r);
+    const float4* z4 = reinterpret_cast<const float4*>(z);
+    const float4* q4 = reinterpret_cast<const float4*>(q);
     double rz = 0.0, zq = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 3 * vol;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
          i += (long long)gridDim.x * blockDim.x) {
-        const float zv = z[i];
-        rz = fma((double)r[i], (double)zv, rz);
-        zq = fma((double)zv, (double)q[i], zq);
+        const float4 a = r4[i], b = z4[i], c4 = q4[i];
+        rz += (double)fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+        zq += (double)fmaf(b.x, c4.x, fmaf(b.y, c4.y, fmaf(b.z, c4.z, b.w * c4.w)));
     }
     double v[2] = {rz, zq};
     if (grid_sum<2>(red, v, sh, out) && threadIdx.x == 0) {
@@ -446,6 +450,8 @@ void destroy_mg(to3d_ctx* c) {
 // Build the level hierarchy once per context (coarse contexts, buffers, maps).
 static to3d_status ensure_mg(to3d_ctx* c) {
     if (c->mg) return TO3D_OK;
+    if (c->g.ny > 65535 || c->g.nz > 65535)
+        return set_err(c, TO3D_EINVAL, "multigrid: more than 65535 nodes along y or z");
     Mg* m = new (std::nothrow) Mg();
     if (!m) return set_err(c, TO3D_ENOMEM, "multigrid");
     c->mg = m;
@@ -582,11 +588,11 @@ static void cycle_launch(to3d_ctx* c, Mg* m, cudaStream_t s, size_t l, const flo
     Level& C = m->lv[l + 1];
     to3d_ctx* kc = C.ctx;
     op();
-    k_restrict<<<(unsigned)((kc->g.nnode + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+    k_restrict<<<dim3((kc->g.nx + 63) / 64, kc->g.ny, kc->g.nz), 64, 0, s>>>(
         k->g, k->px, vol, b, L.t, k->maskp, kc->g, kc->px, kc->vol, kc->maskp, kc->r32, ss);
     c->launches++;
     cycle_launch(c, m, s, l + 1, kc->r32, ss);
-    k_prolong<<<(unsigned)((k->g.nnode + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+    k_prolong<<<dim3((k->g.nx + 127) / 128, k->g.ny, k->g.nz), 128, 0, s>>>(
         k->g, k->px, vol, k->maskp, L.z, kc->g, kc->px, kc->vol, C.z, ss);
     c->launches++;
     op();
@@ -645,14 +651,18 @@ namespace to3d {
 // One inner iteration: z = V r (cycle on ctx->r32), rz and beta, the fused
 // tensor-core kernel p_new = z + beta p_old, q = K p_new, alpha = rz / p.q,
 // then d += alpha p_new, r -= alpha q and |r|^2 (no Jacobi dot).
-static void mgpcg_iter(to3d_ctx* c, Mg* m, cudaStream_t s, int prec, int parity) {
+// ev0/ev1 (may be null): external events recorded around the fused kernel.
+static void mgpcg_iter(to3d_ctx* c, Mg* m, cudaStream_t s, int prec, int parity,
+                       cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
     cycle_launch(c, m, s, 0, c->r32, c->ss);
     k_pcg_dots<<<nblocks(3 * c->vol), kThreads, 0, s>>>(c->vol, c->r32, m->lv[0].z, c->q32, c->red,
                                                         c->ss);
     c->launches++;
     float* p_new = parity ? c->p32b : c->p32a;
     const CUtensorMap& tp = parity ? c->tm_pa : c->tm_pb;
+    if (ev0) cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal);
     launch_matvec_tc_io(c, s, prec, true, m->lv[0].tm_z, tp, m->tm_ones, p_new, c->q32, c->ss);
+    if (ev1) cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal);
     launch_pcg32_update_mode(c, s, p_new, 0);
 }
 
@@ -668,7 +678,17 @@ static to3d_status mgpcg_chunk(to3d_ctx* c, Mg* m, int prec, int n) {
             cudaGraph_t gr;
             const long long l0 = c->launches;
             MG_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-            for (int i = 0; i < n; ++i) mgpcg_iter(c, m, c->cap_stream, prec, i & 1);
+            c->kslots[0] = 0;
+            for (int i = 0; i < n; ++i) {
+                cudaEvent_t e0 = nullptr, e1 = nullptr;
+                if (i % 4 == 0 && c->kslots[0] < to3d_ctx::kTimedSlots) {
+                    const int sl = c->kslots[0]++;
+                    e0 = c->kev[0][2 * sl];
+                    e1 = c->kev[0][2 * sl + 1];
+                    c->kslot_iter[0][sl] = i;
+                }
+                mgpcg_iter(c, m, c->cap_stream, prec, i & 1, e0, e1);
+            }
             MG_CK(cudaStreamEndCapture(c->cap_stream, &gr));
             MG_CK(cudaGraphInstantiate(&m->pcg, gr, 0));
             cudaGraphDestroy(gr);
@@ -709,9 +729,12 @@ to3d_status solve_dc_mg(to3d_ctx* c, const double* f, double fnorm, to3d_solve_i
         k_pcg_init<<<nblocks(c->g.nnode), kThreads, 0, c->stream>>>(
             c->g, c->px, c->vol, c->r, scale, c->nodemask, c->r32, c->d32, c->p32b, c->q32, c->red, c->ss);
         c->launches++;
+        int it0 = 0;
         for (;;) {
             if ((st = mgpcg_chunk(c, m, prec, kMgChunk))) return st;
             if ((st = sync_solver_scalars(c))) return st;
+            accumulate_tc_times(c, it0, c->ss_h->it);
+            it0 = c->ss_h->it;
             if (c->ss_h->done) break;
         }
         const int its = c->ss_h->it;
