@@ -87,6 +87,7 @@ struct Mg {
     double* dots = nullptr;
     double* dots_h = nullptr;
     float* ones = nullptr;            // per-node scaling 1 (fused direction p = z + beta p)
+    float* ke32 = nullptr;            // unit KE in FP32 (coarsest-level sweeps)
     CUtensorMap tm_ones;
     cudaGraphExec_t pcg = nullptr;    // chunk of inner MG-PCG iterations
     int pcg_prec = -1, pcg_n = 0;
@@ -416,6 +417,81 @@ __global__ void k_pow_final(const double* __restrict__ out, double w, double mar
     lam_out[l] = lam_ok;
 }
 
+// The coarsest level's Jacobi sweeps in one CTA (grids of at most
+// kCoarseNodes nodes): b, D^-1, the clamp bits and z in shared memory, the
+// operator element by element in FP32 on the CUDA cores (24 x 24 products,
+// shared-memory atomics into the nodes).  Same sweeps as the per-kernel
+// form: z = w D^-1 b, then sweeps - 1 times z += w D^-1 (b - K z).
+constexpr int kCoarseNodes = 1024;
+constexpr int kCoarseThreads = 256;
+
+__global__ void __launch_bounds__(kCoarseThreads)
+    k_coarse_sweeps(const Grid g, int px, long long vol, int pex, const float* __restrict__ b,
+                    const float* __restrict__ E32, const float* __restrict__ dinv,
+                    const uint8_t* __restrict__ maskp, const float* __restrict__ KE,
+                    const float* __restrict__ wdev, int l, int sweeps, float* __restrict__ z,
+                    const SolverScalars* ss) {
+    if (skip(ss)) return;
+    __shared__ float Ks[576];
+    __shared__ float zs[3 * kCoarseNodes], ts[3 * kCoarseNodes], bs[3 * kCoarseNodes];
+    __shared__ float ds[kCoarseNodes];
+    __shared__ uint8_t ms[kCoarseNodes];
+    const int nn = (int)g.nnode, tid = threadIdx.x;
+    const float w = wdev[l];
+    for (int i = tid; i < 576; i += blockDim.x) Ks[i] = KE[i];
+    for (int n = tid; n < nn; n += blockDim.x) {
+        const int i = n % g.nx, jk = n / g.nx;
+        const long long p = i + (long long)px * jk;
+        const uint8_t m = maskp[p];
+        const float d = w * dinv[p];
+        ds[n] = d;
+        ms[n] = m;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float bv = b[c * vol + p];
+            bs[3 * n + c] = bv;
+            zs[3 * n + c] = ((m >> c) & 1) ? 0.f : d * bv;
+        }
+    }
+    __syncthreads();
+    for (int sw = 1; sw < sweeps; ++sw) {
+        for (int i = tid; i < 3 * nn; i += blockDim.x) ts[i] = 0.f;
+        __syncthreads();
+        for (long long e = tid; e < g.nel; e += blockDim.x) {
+            const int ei = (int)(e % g.nelx), ej = (int)((e / g.nelx) % g.nely),
+                      ek = (int)(e / ((long long)g.nelx * g.nely));
+            int nd[8];
+            float ze[24];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) {
+                nd[a] = (ei + (a & 1)) + g.nx * ((ej + ((a >> 1) & 1)) + g.ny * (ek + (a >> 2)));
+#pragma unroll
+                for (int c = 0; c < 3; ++c) ze[3 * a + c] = zs[3 * nd[a] + c];
+            }
+            const float Ee = E32[ei + (long long)pex * (ej + (long long)g.nely * ek)];
+#pragma unroll 4
+            for (int r = 0; r < 24; ++r) {
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < 24; ++k) acc = fmaf(Ks[r * 24 + k], ze[k], acc);
+                atomicAdd(&ts[3 * nd[r / 3] + r % 3], Ee * acc);
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < 3 * nn; i += blockDim.x) {
+            const int n = i / 3, c = i - 3 * n;
+            if (!((ms[n] >> c) & 1)) zs[i] = fmaf(ds[n], bs[i] - ts[i], zs[i]);
+        }
+        __syncthreads();
+    }
+    for (int n = tid; n < nn; n += blockDim.x) {
+        const int i = n % g.nx, jk = n / g.nx;
+        const long long p = i + (long long)px * jk;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) z[c * vol + p] = zs[3 * n + c];
+    }
+}
+
 static unsigned nblocks(long long n) {
     long long b = (n + kThreads - 1) / kThreads;
     if (b > 152 * 8) b = 152 * 8;
@@ -439,7 +515,7 @@ void destroy_mg(to3d_ctx* c) {
         if (l > 0) to3d_destroy(m->lv[l].ctx);
     }
     for (auto& s : m->snaps) cudaFree(s.r);
-    void* ptrs[] = {m->wdev, m->lamdev, m->z64, m->rprev, m->dots, m->ones};
+    void* ptrs[] = {m->wdev, m->lamdev, m->z64, m->rprev, m->dots, m->ones, m->ke32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (m->dots_h) cudaFreeHost(m->dots_h);
@@ -512,6 +588,12 @@ static to3d_status ensure_mg(to3d_ctx* c) {
     MG_CK(cudaMalloc(&m->wdev, sizeof(float) * kMaxLevels));
     MG_CK(cudaMalloc(&m->lamdev, sizeof(double) * kMaxLevels));
     {
+        float ke[576];
+        for (int i = 0; i < 576; ++i) ke[i] = (float)c->ke.v[i];
+        MG_CK(cudaMalloc(&m->ke32, sizeof(ke)));
+        MG_CK(cudaMemcpy(m->ke32, ke, sizeof(ke), cudaMemcpyHostToDevice));
+    }
+    {
         double l1 = 0.0;
         for (int a = 0; a < 24; ++a) {
             double row = 0.0;
@@ -574,6 +656,13 @@ static void cycle_launch(to3d_ctx* c, Mg* m, cudaStream_t s, size_t l, const flo
         launch_matvec_tc_io(k, s, m->prec, false, k->tm_r, L.tm_z, k->tm_d, nullptr, L.t, ss);
         if (k != c) c->launches++;
     };
+    if (l + 1 == m->lv.size() && k->g.nnode <= kCoarseNodes) {
+        k_coarse_sweeps<<<1, kCoarseThreads, 0, s>>>(k->g, k->px, vol, k->pex, b, k->E32, k->dinv32,
+                                                     k->maskp, m->ke32, m->wdev, (int)l, m->sweeps,
+                                                     L.z, ss);
+        c->launches++;
+        return;
+    }
     k_jacobi0<<<nblocks(vol), kThreads, 0, s>>>(vol, b, k->dinv32, k->maskp, m->wdev, (int)l, L.z, ss);
     c->launches++;
     if (l + 1 == m->lv.size()) {
