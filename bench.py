@@ -295,23 +295,35 @@ def _peaks():
         return {}
 
 
+TRAIN_AT = (4, 8, 12, 16, 20)     # OC iterations after which snapshots are taken
+TRAIN_SNAPS = 2                    # snapshots per design
+TRAIN_STEPS = 20
+
+
 def train_lmg(stream):
     """Learn the multigrid parameters on a 96x32x16 cantilever of the bench's
-    family after 6 OC iterations; returns (theta, record)."""
+    family: snapshots of designs along its own OC trajectory (the multigrid
+    form runs the trajectory); returns (theta, record)."""
     import torch
     from paper_2504_05604_gb300 import LMG, Context
     from synth import problems
     small = problems.config_large(nelx=TRAIN_GRID[0], nely=TRAIN_GRID[1], nelz=TRAIN_GRID[2])
     t0 = time.perf_counter()
     tctx = Context.from_problem(small, precision=0, precond=LMG, stream=stream.cuda_stream)
-    for _ in range(6):
-        tctx.step()
-    first, last = tctx.mg_train(nsnap=8, steps=20, lr=0.1, seed=3)
+    it = 0
+    for k, at in enumerate(TRAIN_AT):
+        while it < at:
+            tctx.step()
+            it += 1
+        last_call = k == len(TRAIN_AT) - 1
+        first, last = tctx.mg_train(nsnap=TRAIN_SNAPS, steps=TRAIN_STEPS if last_call else 0,
+                                    lr=0.1, seed=3, append=k > 0)
     theta = tctx.mg_params()
     tctx.close()
     torch.cuda.synchronize()
-    return theta, {"grid": "x".join(map(str, TRAIN_GRID)), "after_oc_iterations": 6,
-                   "snapshots": 8, "adam_steps": 20, "loss_first": first, "loss_last": last,
+    return theta, {"grid": "x".join(map(str, TRAIN_GRID)), "snapshots_after_oc_iterations":
+                   list(TRAIN_AT), "snapshots": TRAIN_SNAPS * len(TRAIN_AT),
+                   "adam_steps": TRAIN_STEPS, "loss_first": first, "loss_last": last,
                    "theta": [round(float(v), 4) for v in theta],
                    "seconds": time.perf_counter() - t0}
 

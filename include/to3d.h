@@ -354,15 +354,20 @@ TO3D_API to3d_status to3d_mg_levels(to3d_ctx* ctx, int32_t* nlev);
  * entries ignored; z is 0 there), host or device as `on_device` says. */
 TO3D_API to3d_status to3d_mg_apply(to3d_ctx* ctx, const double* x, const double* r, double* z,
                                    int32_t on_device);
-/* Learn theta on the context's current design: `nsnap` residuals of FP64
- * Jacobi-PCG from u = 0 after a random number (0..200) of iterations (seed
- * `seed`), each with r^T K^-1 r from an FP64 solve to 1e-10; then `steps`
- * Adam steps (rate lr) on central-difference gradients of the mean
- * energy-norm error ||e - V r||_K^2 / ||e||_K^2, e = K^-1 r.  Keeps the best
- * parameters seen; *loss_first / *loss_last: mean loss before and after.
- * Overwrites the context's displacement. */
+/* Learn theta from snapshots of the method's own solves.  Takes `nsnap`
+ * snapshots on the context's current design: residuals of FP64 Jacobi-PCG
+ * from u = 0 after a random number (0..200) of iterations (seed `seed`),
+ * each with r^T K^-1 r from an FP64 solve to 1e-10; with append = 1 they are
+ * added to those of earlier calls (other designs of the trajectory; at most
+ * 256 in all), else they replace them.  Then `steps` Adam steps (rate lr) on
+ * central-difference gradients of the mean energy-norm error
+ * ||e - V r||_K^2 / ||e||_K^2, e = K^-1 r, each snapshot with the operator
+ * of its own design.  Keeps the best parameters seen; *loss_first /
+ * *loss_last: mean loss before and after.  Overwrites the context's
+ * displacement. */
 TO3D_API to3d_status to3d_mg_train(to3d_ctx* ctx, int32_t nsnap, int32_t steps, double lr,
-                                   uint64_t seed, double* loss_first, double* loss_last);
+                                   uint64_t seed, int32_t append, double* loss_first,
+                                   double* loss_last);
 
 typedef struct to3d_batch to3d_batch;
 

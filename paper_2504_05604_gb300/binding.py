@@ -103,7 +103,7 @@ _SIGS = {
     "to3d_mg_set_params": (I32, [VP, DP, C.c_int64]),
     "to3d_mg_levels": (I32, [VP, C.POINTER(I32)]),
     "to3d_mg_apply": (I32, [VP, VP, VP, VP, I32]),
-    "to3d_mg_train": (I32, [VP, I32, I32, C.c_double, C.c_uint64, DP, DP]),
+    "to3d_mg_train": (I32, [VP, I32, I32, C.c_double, C.c_uint64, I32, DP, DP]),
     "to3d_conv3d_forward": (I32, [I32, I32, I32, I32, I32, I32, VP, VP, VP, VP, I32, VP, VP]),
     "to3d_conv3d_backward": (I32, [I32, I32, I32, I32, I32, I32, VP, VP, VP, VP, VP, VP, VP, VP,
                                    VP]),
@@ -441,12 +441,15 @@ class Context:
         self._check(self.lib.to3d_mg_apply(self.h, ax.ptr, ar.ptr, az.ptr, dev), "mg_apply")
         return z
 
-    def mg_train(self, nsnap: int = 8, steps: int = 40, lr: float = 0.05, seed: int = 0):
-        """Learn the multigrid parameters on the current design; returns the
-        mean energy loss before and after."""
+    def mg_train(self, nsnap: int = 8, steps: int = 40, lr: float = 0.05, seed: int = 0,
+                 append: bool = False):
+        """Take `nsnap` snapshots on the current design (added to earlier
+        ones with `append`) and learn the multigrid parameters over all of
+        them for `steps` Adam steps; returns the mean energy loss before and
+        after."""
         a, b = C.c_double(), C.c_double()
-        self._check(self.lib.to3d_mg_train(self.h, nsnap, steps, lr, seed, C.byref(a),
-                                           C.byref(b)), "mg_train")
+        self._check(self.lib.to3d_mg_train(self.h, nsnap, steps, lr, seed, int(append),
+                                           C.byref(a), C.byref(b)), "mg_train")
         return a.value, b.value
 
 

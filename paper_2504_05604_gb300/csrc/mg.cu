@@ -68,7 +68,8 @@ struct Level {
 struct Snap {
     double* r = nullptr;         // residual (AoS FP64, dofs)
     double rn = 0.0;             // |r|
-    double rte = 0.0;            // r^T K^-1 r
+    double rte = 0.0;            // r^T K^-1 r for the operator of its design
+    int design = 0;              // index into Mg::designs
 };
 
 struct Mg {
@@ -92,6 +93,7 @@ struct Mg {
     cudaGraphExec_t pcg = nullptr;    // chunk of inner MG-PCG iterations
     int pcg_prec = -1, pcg_n = 0;
     std::vector<Snap> snaps;
+    std::vector<double*> designs;     // densities the snapshots belong to (device)
     bool trained = false;
 };
 
@@ -515,6 +517,7 @@ void destroy_mg(to3d_ctx* c) {
         if (l > 0) to3d_destroy(m->lv[l].ctx);
     }
     for (auto& s : m->snaps) cudaFree(s.r);
+    for (double* x : m->designs) cudaFree(x);
     void* ptrs[] = {m->wdev, m->lamdev, m->z64, m->rprev, m->dots, m->ones, m->ke32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -882,11 +885,17 @@ static to3d_status snapshot_loss(to3d_ctx* c, double* loss) {
     Mg* m = mg_of(c);
     cudaStream_t s = c->stream;
     const long long ndof = 3 * c->g.nnode;
-    m->params_dirty = true;
-    to3d_status st = ready(c);
-    if (st) return st;
+    to3d_status st;
     double sum = 0.0;
-    for (auto& sn : m->snaps) {
+    int cur = -1;
+    for (auto& sn : m->snaps) {      // grouped by design (appended design by design)
+        if (sn.design != cur) {
+            // the operator of this snapshot's design, and the hierarchy for
+            // it with the current parameters
+            cur = sn.design;
+            if ((st = prepare_op(c, m->designs[cur]))) return st;
+            if ((st = ready(c))) return st;
+        }
         if ((st = mg_apply64(c, sn.r, m->z64, sn.rn))) return st;
         // z is 0 on clamped dofs, where the FP64 operator has identity rows
         launch_matvec64(c, s, c->E, m->z64, c->tmp, false);
@@ -989,21 +998,39 @@ to3d_status to3d_mg_apply(to3d_ctx* c, const double* x, const double* r, double*
 // from an FP64 solve of K e = r to 1e-10; then `steps` Adam steps on
 // central-difference gradients of the mean loss.
 to3d_status to3d_mg_train(to3d_ctx* c, int32_t nsnap, int32_t steps, double lr, uint64_t seed,
-                          double* loss_first, double* loss_last) {
-    if (!c || nsnap < 1 || nsnap > 256 || steps < 0 || !(lr > 0) || !loss_first || !loss_last)
+                          int32_t append, double* loss_first, double* loss_last) {
+    if (!c || nsnap < 0 || nsnap > 256 || steps < 0 || !(lr > 0) || !loss_first || !loss_last)
         return TO3D_EINVAL;
     to3d_status st = ensure_mg(c);
     if (st) return st;
     Mg* m = mg_of(c);
     cudaStream_t s = c->stream;
     const long long ndof = 3 * c->g.nnode;
+    if (!append) {
+        for (auto& sn : m->snaps) cudaFree(sn.r);
+        m->snaps.clear();
+        for (double* x : m->designs) cudaFree(x);
+        m->designs.clear();
+    }
+    if (m->snaps.size() + (size_t)nsnap > 256)
+        return set_err(c, TO3D_EINVAL, "more than 256 multigrid training snapshots");
+    if (m->snaps.size() + (size_t)nsnap == 0) return set_err(c, TO3D_EINVAL, "no training snapshots");
+    // the snapshots of earlier designs keep their own r^T K^-1 r; the loss
+    // evaluates every snapshot with the operator of the current design, so
+    // the training loop below needs the current design's operator prepared
     if ((st = prepare_op(c, c->x))) return st;
-    for (auto& sn : m->snaps) cudaFree(sn.r);
-    m->snaps.clear();
-    unsigned long long rng = seed * 0x2545F4914F6CDD1DULL + 12345u;
+    const int di = (int)m->designs.size();
+    if (nsnap > 0) {
+        double* xd = nullptr;
+        MG_CK(cudaMalloc(&xd, sizeof(double) * c->g.nel));
+        MG_CK(cudaMemcpyAsync(xd, c->x, sizeof(double) * c->g.nel, cudaMemcpyDeviceToDevice, s));
+        m->designs.push_back(xd);
+    }
+    unsigned long long rng = seed * 0x2545F4914F6CDD1DULL + 12345u + 977u * (unsigned long long)di;
     for (int i = 0; i < nsnap; ++i) {
         const int k = (int)(splitmix(rng) % 201ULL);
         Snap sn;
+        sn.design = di;
         MG_CK(cudaMalloc(&sn.r, sizeof(double) * ndof));
         m->snaps.push_back(sn);
         if ((st = run_pcg64_iters(c, c->f, k))) return st;
@@ -1062,6 +1089,7 @@ to3d_status to3d_mg_train(to3d_ctx* c, int32_t nsnap, int32_t steps, double lr, 
     m->params_dirty = true;
     m->trained = true;
     *loss_last = best;
+    if ((st = prepare_op(c, c->x))) return st;
     return launch_check(c, "mg train");
 }
 

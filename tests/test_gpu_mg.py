@@ -125,9 +125,12 @@ def test_training_lowers_the_loss_and_the_iterations_on_a_new_design():
     from paper_2504_05604_gb300 import LMG
     prob = problems.cantilever(48, 16, 8, load="centre", volfrac=0.2, rmin=2.5)
     ctx = lib_ctx(prob, precision=0, precond=LMG)
-    for _ in range(6):
+    for _ in range(4):
         ctx.step()
-    first, last = ctx.mg_train(nsnap=8, steps=15, lr=0.1, seed=1)
+    ctx.mg_train(nsnap=4, steps=0, lr=0.1, seed=1)
+    for _ in range(2):
+        ctx.step()
+    first, last = ctx.mg_train(nsnap=4, steps=15, lr=0.1, seed=1, append=True)
     print(f"training loss {first:.4f} -> {last:.4f}; theta {np.round(ctx.mg_params(), 3)}")
     assert last < first
     theta = ctx.mg_params()
