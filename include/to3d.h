@@ -101,7 +101,7 @@ typedef struct {
                             * context has timed a plain solve of its own (0:
                             * no such bound until then)                       */
     int32_t mg_sweeps;   /* TO3D_LMG: Jacobi sweeps on the coarsest level
-                          * (0: 16)                                           */
+                          * (0: 6)                                            */
     int32_t reserved[4];
 } to3d_params;
 
@@ -328,7 +328,7 @@ TO3D_API to3d_status to3d_conv3d_backward(int32_t Z, int32_t Y, int32_t X, int32
  *              modulus);
  *   transfer   trilinear prolongation P, restriction P^T, clamped dofs 0;
  *   smoother   damped Jacobi, one sweep before and one after the coarse
- *              correction, params.mg_sweeps sweeps (default 16) on the
+ *              correction, params.mg_sweeps sweeps (default 6) on the
  *              coarsest level; damping w_l * 2 / lam_l, lam_l = min(1.2 rq,
  *              l1) with rq the Rayleigh quotient of D^-1 K after 16 power
  *              steps from a fixed hashed start and l1 = max_a sum_b

@@ -78,7 +78,7 @@ struct Mg {
     float* wdev = nullptr;            // damping per level (device)
     double* lamdev = nullptr;         // eigenvalue bound per level (device)
     double l1 = 59.0 / 11.0;          // max_a sum_b |KE_ab| / KE_aa
-    int sweeps = 16;
+    int sweeps = 6;
     int prec = TO3D_BF16_DC;
     cudaGraphExec_t cycle = nullptr;  // ctx->r32 -> lv[0].z, captured
     long long cycle_launches = 0;     // kernels in one cycle
@@ -535,7 +535,7 @@ static to3d_status ensure_mg(to3d_ctx* c) {
     if (!m) return set_err(c, TO3D_ENOMEM, "multigrid");
     c->mg = m;
     default_theta(m->theta);
-    m->sweeps = c->prm.mg_sweeps > 0 ? c->prm.mg_sweeps : 16;
+    m->sweeps = c->prm.mg_sweeps > 0 ? c->prm.mg_sweeps : 6;
     m->prec = c->prm.precision == TO3D_F64 ? TO3D_BF16_DC : c->prm.precision;
     // clamp masks on the host, level by level
     const Grid& g0 = c->g;

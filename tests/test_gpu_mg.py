@@ -26,7 +26,7 @@ def per_level(theta, nlev):
     return w, q, s
 
 
-def oracle_cycle(prob, x, r, theta, sweeps=16):
+def oracle_cycle(prob, x, r, theta, sweeps=6):
     KE = fem.element_stiffness(prob.nu)
     E = fem.simp_modulus(x, prob.penal, prob.E0, prob.Emin)
     lv = mg.hierarchy(prob.nelx, prob.nely, prob.nelz, prob.fixed)
