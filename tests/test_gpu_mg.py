@@ -152,4 +152,4 @@ def test_training_lowers_the_loss_and_the_iterations_on_a_new_design():
     jac.close()
     print(f"held-out design: init {its['init']}, trained {its['trained']}, Jacobi {ij['iters']}")
     assert its["trained"] <= its["init"]
-    assert its["trained"] * 4 < ij["iters"]
+    assert its["trained"] * 3 < ij["iters"]
