@@ -102,7 +102,13 @@ typedef struct {
                             * no such bound until then)                       */
     int32_t mg_sweeps;   /* TO3D_LMG: Jacobi sweeps on the coarsest level
                           * (0: 6)                                            */
-    int32_t reserved[4];
+    int32_t fp64_tc;     /* 1: every FP64 K p (the FP64 forms' matvec, the
+                          * defect correction's residual, flexible CG) on the
+                          * tensor cores by exact integer slicing of p (FP64
+                          * accuracy; needs a nu whose lambda / mu is a small
+                          * rational, else the CUDA-core FP64 kernel runs);
+                          * 0 (default): the CUDA-core FP64 kernel            */
+    int32_t reserved[3];
 } to3d_params;
 
 typedef struct {

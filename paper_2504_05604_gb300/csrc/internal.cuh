@@ -122,6 +122,8 @@ struct to3d_ctx {
     uint8_t* tcB = nullptr;               // tensor-core B operand images (BF16 then FP16)
     bool tc_split = false;                // B = [A_lam; A_mu] (N = 48) instead of one matrix
     float tc_cscale = 1.f;                // scale of the combined integer B
+    double tc_cscale_d = 1.0;             // the same scale in FP64
+    double tc_bmax = 0.0;                 // max |B| of the combined integer B
     int tc_lz = 20;                       // node layers per z segment of a tile
     int tc_grid = 608;                    // persistent CTAs
     long long ndesign = 0;                // number of design (non-passive) elements
@@ -192,6 +194,10 @@ void launch_mask_copy(to3d_ctx* c, cudaStream_t s, const double* src, double* ds
 
 // matvec_tc.cu
 void launch_matvec_tc(to3d_ctx* c, cudaStream_t s, int prec, bool fused, int parity);
+// matvec_x64.cu: FP64-accurate K p on the tensor cores (integer slicing)
+bool matvec_x64_available(const to3d_ctx* c);
+void launch_matvec_x64(to3d_ctx* c, cudaStream_t s, const double* E, const double* p, double* y,
+                       bool dot_pq);
 void launch_matvec_tc_io(to3d_ctx* c, cudaStream_t s, int prec, bool fused, const CUtensorMap& tr,
                          const CUtensorMap& tp, const CUtensorMap& td, float* p_new, float* q,
                          SolverScalars* ss);

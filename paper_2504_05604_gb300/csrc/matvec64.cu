@@ -210,6 +210,10 @@ void launch_mask_copy(to3d_ctx* c, cudaStream_t s, const double* src, double* ds
 
 void launch_matvec64(to3d_ctx* c, cudaStream_t s, const double* E, const double* p, double* y,
                      bool dot_pq) {
+    if (c->prm.fp64_tc && matvec_x64_available(c)) {
+        launch_matvec_x64(c, s, E, p, y, dot_pq);
+        return;
+    }
     const Grid& g = c->g;
     dim3 blk(MV_TX, MV_TY, MV_TZ);
     dim3 grd((g.nx + MV_TX - 1) / MV_TX, (g.ny + MV_TY - 1) / MV_TY, (g.nz + MV_TZ - 1) / MV_TZ);

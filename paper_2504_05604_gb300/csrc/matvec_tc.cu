@@ -758,6 +758,11 @@ bool prepare_tc_operands(to3d_ctx* c) {
     }
     c->tc_split = (cb == 0);
     c->tc_cscale = c->tc_split ? 1.0f : (float)(c->kes.c_mu / cb);
+    c->tc_cscale_d = c->tc_split ? 1.0 : c->kes.c_mu / cb;
+    c->tc_bmax = 0.0;
+    if (!c->tc_split)
+        for (int k = 0; k < 576; ++k)
+            c->tc_bmax = std::fmax(c->tc_bmax, std::fabs((double)ca * c->kes.a_lam[k] + (double)cb * c->kes.a_mu[k]));
     const int nmma = c->tc_split ? 64 : 32;
     // the spare row 24 (combined) or 48 (split) copies operand column 24 (the
     // per-element exponent code of the FP16 form) into the accumulator
