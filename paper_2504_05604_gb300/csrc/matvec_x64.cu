@@ -273,7 +273,12 @@ __global__ void __launch_bounds__(X64_THREADS, 2) k_matvec_x64(const __grid_cons
         // the next layer overwrites the staged plane kk and the output buffer
         // of layer kk - 1 only after every thread is past this point
         __syncthreads();
-        if (s_fail) break;
+        if (s_fail) {
+            // after a timeout: the MMAs of this layer must finish before TMEM
+            // is freed (bounded as well)
+            if (tid == 0) tc::mbar_wait_sleep_bounded(bar, phase ^ 1u, X64_WAIT_POLLS, 1000u);
+            break;
+        }
     }
     __syncthreads();
     if (s_fail && tid == 0) atomicExch(a.err, (int)TO3D_ETIMEOUT);
