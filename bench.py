@@ -78,6 +78,9 @@ def parse():
                     help="residual-replacement factor of the defect-correction forms "
                          "(default 0.01 with the multigrid, 0.3 with Jacobi)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the comparison forms")
+    ap.add_argument("--fp64-cuda-cores", action="store_true",
+                    help="FP64 K p of the chosen and learned forms on the CUDA cores instead of "
+                         "the sliced tensor-core kernel")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--unet", action="store_true",
@@ -412,8 +415,10 @@ def ours(args):
     stream = torch.cuda.Stream(device=dev)
     lmg = args.precond == "lmg"
     theta, train = (train_lmg(stream) if lmg else (None, None))
+    # fp64_tc: the FP64 residual replacements on the tensor cores by exact
+    # integer slicing (FP64 accuracy)
     form = dict(precision=args.precision, precond=LMG if lmg else JACOBI,
-                inner_rtol=args.inner_rtol)
+                inner_rtol=args.inner_rtol, fp64_tc=0 if args.fp64_cuda_cores else 1)
 
     def make_ctx():
         c = Context.from_problem(prob, stream=stream.cuda_stream, **form)
@@ -501,11 +506,15 @@ def ours(args):
     # the other forms, one OC iteration from each of the three designs
     samples = [(f"after OC iteration {args.warmup + k}", xs[i], us[i])
                for i, k in enumerate((0, mid, args.steps))]
-    fp64 = learned = jacobi_dc = None
+    fp64 = learned = jacobi_dc = fp64_sliced = None
     if not args.no_fp64:
         fp64 = form_on_designs(prob, stream, samples, precision=0)
-        learned = form_on_designs(prob, stream, samples, precision=0, precond=LMG, theta=theta)
+        learned = form_on_designs(prob, stream, samples, precision=0, precond=LMG, theta=theta,
+                                  fp64_tc=form["fp64_tc"])
         jacobi_dc = form_on_designs(prob, stream, samples, precision=1, inner_rtol=0.3)
+        # plain FP64 Jacobi-PCG with the sliced tensor-core FP64 K p, on the
+        # last design only (about half a minute)
+        fp64_sliced = form_on_designs(prob, stream, samples[-1:], precision=0, fp64_tc=1)
     unet = None
     if args.unet:
         unet = unet_leg(prob, stream, xs[2].cpu().numpy(),
@@ -539,7 +548,7 @@ def ours(args):
         "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPES[args.precision],
         "data": "synthetic",
-        "config": dict(workload_config(args, world), form=name,
+        "config": dict(workload_config(args, world), form=name, fp64_tc=form["fp64_tc"],
                        arithmetic=ARITHMETIC[args.precision] + (
                            "; preconditioner: learned multigrid V-cycle (FP32, tensor-core "
                            "operator on every level)" if lmg else "; Jacobi preconditioner"),
@@ -556,6 +565,7 @@ def ours(args):
         "plain_fp64": fp64,
         "learned_fcg": learned,
         "jacobi_dc": jacobi_dc,
+        "plain_fp64_sliced_tc": fp64_sliced,
         "unet_fcg": unet,
         "e2e": e2e,
         "cpu_baseline": cpu,
