@@ -24,8 +24,9 @@
 // time: node planes of p are staged in shared memory (clamped dofs as 0),
 // each thread slices its element into the five A tiles, one thread issues
 // the MMAs into five TMEM accumulators, every thread reads its row back,
-// recombines and scales it, and the owned nodes sum their 8 element
-// contributions from the layer below and this one in FP64.  Clamped dofs
+// recombines and scales it, adds the upper-half outputs of the element
+// below it (carried in registers) to its lower-half ones, and the owned
+// nodes sum the four element columns around them in FP64.  Clamped dofs
 // are identity rows (y = p).  Deterministic, no atomics.
 #include "internal.cuh"
 #include "reduce.cuh"
@@ -38,7 +39,7 @@ constexpr int X64_EX = 16, X64_EY = 8;              // elements per layer
 constexpr int X64_PX = 17, X64_PY = 9;              // staged nodes per plane
 constexpr int X64_PLANE = X64_PX * X64_PY * 3;      // doubles per staged plane
 constexpr int X64_THREADS = 128;
-constexpr int X64_SLICES = 5;
+constexpr int X64_SLICES = 5;        // five accumulators of 32 TMEM columns: 256 allocated, 2 CTAs per SM
 constexpr int X64_TILE = 128 * 64;                  // one 128 x 32 FP16 operand tile
 constexpr uint32_t X64_WAIT_POLLS = 1u << 20;
 static_assert(X64_EX * X64_EY == X64_THREADS, "one element per thread, one MMA row each");
@@ -47,8 +48,8 @@ struct X64Smem {
     static constexpr int A = 0;                                   // 5 tiles
     static constexpr int B = A + X64_SLICES * X64_TILE;           // 32 x 32 FP16
     static constexpr int P = B + 32 * 64;                         // 2 node planes
-    static constexpr int Y = P + 2 * X64_PLANE * 8;               // 2 x [128][24] FP64
-    static constexpr int BAR = Y + 2 * 128 * 24 * 8;
+    static constexpr int Y = P + 2 * X64_PLANE * 8;               // [128][12] FP64
+    static constexpr int BAR = Y + 128 * 12 * 8;
     static constexpr int TADDR = BAR + 8;
     static constexpr int USED = TADDR + 8;
     static constexpr int BYTES = 1024 + USED;
@@ -132,6 +133,9 @@ __global__ void __launch_bounds__(X64_THREADS, 2) k_matvec_x64(const __grid_cons
 
     const int ei = tid % X64_EX, ej = tid / X64_EX;
     double dot = 0.0;
+    double carry[12];          // upper-half outputs of this column's element below
+#pragma unroll
+    for (int i = 0; i < 12; ++i) carry[i] = 0.0;
     uint32_t phase = 0;
     load_plane(k0 - 1, (k0 - 1) & 1);
     for (int kk = k0 - 1; kk < k0 + nown; ++kk) {
@@ -144,53 +148,49 @@ __global__ void __launch_bounds__(X64_THREADS, 2) k_matvec_x64(const __grid_cons
         // e_max the largest biased exponent of the element, an entry of
         // biased exponent e and 53-bit significand m is m * 2^(e - 1075), and
         // V = rint(m * 2^(e - e_max - 2)), |V| <= 2^51; the scale is
-        // 2^(e_max - 1073).
-        unsigned long long bits[24];
-        int emax = 1;
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
+        // 2^(e_max - 1073).  Two passes over the staged planes keep the
+        // register count low.
+        auto entry = [&](int i) -> unsigned long long {
+            const int b = i / 3, c = i - 3 * b;
             const double* src = sP + ((kk + (b >> 2)) & 1) * X64_PLANE +
                                 3 * ((ei + (b & 1)) + X64_PX * (ej + ((b >> 1) & 1)));
+            return valid ? (unsigned long long)__double_as_longlong(src[c]) : 0ull;
+        };
+        int emax = 1;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const unsigned long long u = valid ? (unsigned long long)__double_as_longlong(src[c]) : 0ull;
-                bits[3 * b + c] = u;
-                emax = max(emax, (int)((u >> 52) & 0x7FF));
+        for (int i = 0; i < 24; ++i) emax = max(emax, (int)((entry(i) >> 52) & 0x7FF));
+#pragma unroll
+        for (int kc = 0; kc < 3; ++kc) {
+            long long V[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const unsigned long long u = entry(8 * kc + q);
+                int e = (int)((u >> 52) & 0x7FF);
+                unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+                if (e) m |= 1ull << 52;
+                else e = 1;
+                const int sh = emax - e + 2;
+                const unsigned long long mag = sh >= 63 ? 0ull : (m + (1ull << (sh - 1))) >> sh;
+                V[q] = (u >> 63) ? -(long long)mag : (long long)mag;
             }
-        }
-        long long V[24];
 #pragma unroll
-        for (int i = 0; i < 24; ++i) {
-            const unsigned long long u = bits[i];
-            int e = (int)((u >> 52) & 0x7FF);
-            unsigned long long m = u & 0xFFFFFFFFFFFFFull;
-            if (e) m |= 1ull << 52;
-            else e = 1;
-            const int sh = emax - e + 2;
-            const unsigned long long mag = sh >= 63 ? 0ull : (m + (1ull << (sh - 1))) >> sh;
-            V[i] = (u >> 63) ? -(long long)mag : (long long)mag;
-        }
-#pragma unroll
-        for (int s = 0; s < X64_SLICES; ++s) {
-            const int sh = 11 * (X64_SLICES - 1 - s);
-            uint8_t* At = sA + s * X64_TILE;
-#pragma unroll
-            for (int kc = 0; kc < 3; ++kc) {
+            for (int s = 0; s < X64_SLICES; ++s) {
+                const int sh = 11 * (X64_SLICES - 1 - s);
                 uint32_t w[4];
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
                     float f2[2];
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
-                        const long long x = V[8 * kc + 2 * h + q];
-                        const long long m = (x < 0 ? -x : x) >> sh;
-                        const float d = (float)(m & 0x7FF);
-                        f2[q] = x < 0 ? -d : d;
+                        const long long x = V[2 * h + q];
+                        const int d = (int)(((x < 0 ? -x : x) >> sh) & 0x7FF);
+                        f2[q] = (float)(x < 0 ? -d : d);
                     }
                     __half2 hv = __floats2half2_rn(f2[0], f2[1]);
                     w[h] = *reinterpret_cast<uint32_t*>(&hv);
                 }
-                *reinterpret_cast<uint4*>(At + x64_kmaj(tid, 8 * kc)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4*>(sA + s * X64_TILE + x64_kmaj(tid, 8 * kc)) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
         tc::fence_proxy_async_smem();
@@ -213,49 +213,52 @@ __global__ void __launch_bounds__(X64_THREADS, 2) k_matvec_x64(const __grid_cons
         if (!tc::mbar_wait_sleep_bounded(bar, phase, X64_WAIT_POLLS, 1000u)) s_fail = 1;
         phase ^= 1u;
         tc::tc_fence_after();
-        // ---- recombine the slices exactly, scale, keep the element's 24 outputs
-        long long Y[24];
-#pragma unroll
-        for (int i = 0; i < 24; ++i) Y[i] = 0;
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll
-        for (int s = 0; s < X64_SLICES; ++s) {
-            float d0[16], d1[16];
-            tc::tmem_ld16_sync(trow + 32u * s, d0);
-            tc::tmem_ld16_sync(trow + 32u * s + 16u, d1);
-#pragma unroll
-            for (int i = 0; i < 24; ++i) {
-                const float acc = i < 16 ? d0[i] : d1[i - 16];
-                Y[i] = Y[i] * 2048 + (long long)acc;
-            }
-        }
+        // ---- recombine the slices exactly and scale; the lower-half corners
+        // (c = 0) plus the carried upper halves of the element below in this
+        // column give this column's part of node plane kk
         const double Ee = valid ? a.E[elem_id(g, gi, gj, kk)] : 0.0;
         // an Inf or NaN entry (biased exponent 2047) makes the element's
         // outputs NaN, as the FP64 kernel would
         const double scl = emax == 2047 ? __longlong_as_double(0x7FF8000000000000ll)
                                         : ldexp(a.cscale * Ee, emax - 1073);
-        double* yrow = sY + ((kk & 1) * 128 + tid) * 24;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        double* yrow = sY + tid * 12;
 #pragma unroll
-        for (int i = 0; i < 24; ++i) yrow[i] = __ll2double_rn(Y[i]) * scl;
+        for (int half = 0; half < 2; ++half) {     // outputs 0..11 (c = 0), 12..23 (c = 1)
+            long long Y[12];
+#pragma unroll
+            for (int i = 0; i < 12; ++i) Y[i] = 0;
+#pragma unroll
+            for (int s = 0; s < X64_SLICES; ++s) {
+                float d0[16];
+                tc::tmem_ld16_sync(trow + 32u * s + (half ? 8u : 0u), d0);
+#pragma unroll
+                for (int i = 0; i < 12; ++i) Y[i] = Y[i] * 2048 + (long long)__float2int_rn(d0[half ? i + 4 : i]);
+            }
+            if (half == 0) {
+#pragma unroll
+                for (int i = 0; i < 12; ++i) yrow[i] = fma(__ll2double_rn(Y[i]), scl, carry[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 12; ++i) carry[i] = __ll2double_rn(Y[i]) * scl;
+            }
+        }
         tc::tc_fence_before();
         __syncthreads();
-        // ---- owned nodes of plane kk: layer kk - 1 (upper halves) + layer kk (lower halves)
+        // ---- owned nodes of plane kk: the four element columns around them
         if (kk >= k0 && tid < X64_BX * X64_BY) {
             const int ni = 1 + tid % X64_BX, nj = 1 + tid / X64_BX;
             const int gni = i0 - 1 + ni, gnj = j0 - 1 + nj;
             if (gni < g.nx && gnj < g.ny) {
-                const double* cur = sY + (kk & 1) * 128 * 24;
-                const double* prv = sY + ((kk + 1) & 1) * 128 * 24;
                 double s0 = 0.0, s1 = 0.0, s2 = 0.0;
 #pragma unroll
                 for (int b = 0; b < 2; ++b)
 #pragma unroll
                     for (int aa = 0; aa < 2; ++aa) {
-                        const int el = (ni - aa) + X64_EX * (nj - b);
-                        const int lo = 3 * (aa + 2 * b), hi = 3 * (aa + 2 * b + 4);
-                        s0 += cur[el * 24 + lo] + prv[el * 24 + hi];
-                        s1 += cur[el * 24 + lo + 1] + prv[el * 24 + hi + 1];
-                        s2 += cur[el * 24 + lo + 2] + prv[el * 24 + hi + 2];
+                        const double* w = sY + ((ni - aa) + X64_EX * (nj - b)) * 12 + 3 * (aa + 2 * b);
+                        s0 += w[0];
+                        s1 += w[1];
+                        s2 += w[2];
                     }
                 const long long nd = node_id(g, gni, gnj, kk);
                 const uint8_t m = a.nodemask[nd];
@@ -270,8 +273,8 @@ __global__ void __launch_bounds__(X64_THREADS, 2) k_matvec_x64(const __grid_cons
                 if (a.dot_pq) dot += pn[0] * s0 + pn[1] * s1 + pn[2] * s2;
             }
         }
-        // the next layer overwrites the staged plane kk and the output buffer
-        // of layer kk - 1 only after every thread is past this point
+        // the next layer overwrites the staged plane kk and the shared
+        // outputs only after every thread is past this point
         __syncthreads();
         if (s_fail) {
             // after a timeout: the MMAs of this layer must finish before TMEM
