@@ -592,11 +592,21 @@ def batched(args):
     from synth import problems
 
     probs = problems.config_batched(64)
-    # the two-slice operand: on these small, void-riddled grids the single-
-    # slice one stalls the device-side defect correction of some problems
-    prec = args.precision if args.precision in (2, 4) else 2
     stream = torch.cuda.current_stream()
-    b = Batch(probs, precision=prec, inner_rtol=args.inner_rtol)
+    lmg = args.precond == "lmg"
+    if lmg:
+        # the learned multigrid in every problem's graph, with the parameters
+        # learned as for the large workload
+        from paper_2504_05604_gb300 import LMG
+        prec = args.precision
+        theta, _ = train_lmg(torch.cuda.Stream())
+        b = Batch(probs, precision=prec, precond=LMG, inner_rtol=args.inner_rtol)
+        b.set_mg_params(theta)
+    else:
+        # the two-slice operand: on these small, void-riddled grids the single-
+        # slice one stalls the device-side Jacobi defect correction of some problems
+        prec = args.precision if args.precision in (2, 4) else 2
+        b = Batch(probs, precision=prec, inner_rtol=args.inner_rtol)
     for _ in range(args.warmup):
         b.step()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -611,7 +621,10 @@ def batched(args):
     # driven solver, no graphs), the same OC iterations: W untimed, K timed
     t_seq = 0.0
     for pr in probs:
-        c = Context.from_problem(pr, precision=prec, inner_rtol=args.inner_rtol)
+        c = Context.from_problem(pr, precision=prec, inner_rtol=args.inner_rtol,
+                                 precond=(2 if lmg else 0))
+        if lmg:
+            c.set_mg_params(theta)
         for _ in range(args.warmup):
             c.step()
         torch.cuda.synchronize()
@@ -626,7 +639,8 @@ def batched(args):
         "metric": "OC iters/s, 64 seeded uneven cantilevers stepped together",
         "value": 64 * args.steps / (ms / 1000.0), "unit": "problem OC iters/s",
         "elements": nel, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "form": PREC_NAMES[prec], "status": max(r["status"] for rr in recs for r in rr),
+        "form": PREC_NAMES[prec] + ("-lmg" if lmg else ""),
+        "status": max(r["status"] for rr in recs for r in rr),
         "cg_iters_mean": statistics.mean(r["cg_iters"] for rr in recs for r in rr),
         "sequential_single_contexts": {"value": 64 * args.steps / t_seq,
                                        "unit": "problem OC iters/s",

@@ -396,6 +396,11 @@ TO3D_API to3d_status to3d_batch_create(int32_t nprob, const to3d_params* params,
 TO3D_API to3d_status to3d_batch_step(to3d_batch* b, to3d_iter_info* info);
 TO3D_API to3d_status to3d_batch_get_density(to3d_batch* b, int32_t i, double* x, int32_t on_device);
 TO3D_API int32_t to3d_batch_size(const to3d_batch* b);
+/* Learned-multigrid parameters (see to3d_mg_set_params) for every problem of
+ * a batch created with params.precond = TO3D_LMG; the problems' OC-iteration
+ * graphs are captured again.  TO3D_ESTATE if a problem uses another
+ * preconditioner, TO3D_EINVAL for invalid parameters. */
+TO3D_API to3d_status to3d_batch_set_mg_params(to3d_batch* b, const double* theta, int64_t n);
 TO3D_API void to3d_batch_destroy(to3d_batch* b);
 
 /* Failure-detection self-test: one thread waits, with the bounded

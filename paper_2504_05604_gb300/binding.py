@@ -112,6 +112,7 @@ _SIGS = {
     "to3d_batch_step": (I32, [VP, C.POINTER(IterInfo)]),
     "to3d_batch_get_density": (I32, [VP, I32, VP, I32]),
     "to3d_batch_size": (I32, [VP]),
+    "to3d_batch_set_mg_params": (I32, [VP, DP, C.c_int64]),
     "to3d_batch_destroy": (None, [VP]),
 }
 
@@ -580,6 +581,12 @@ class Batch:
         if st != 0:
             raise To3dError(st, "to3d_batch_step")
         return recs
+
+    def set_mg_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        st = self.lib.to3d_batch_set_mg_params(self.h, th.ctypes.data_as(DP), th.size)
+        if st != 0:
+            raise To3dError(st, "to3d_batch_set_mg_params")
 
     def density(self, i):
         out = np.empty(self.nel[i])

@@ -117,6 +117,53 @@ __global__ void k_dc_prepare(const Grid g, int px, long long vol, const double* 
     }
 }
 
+// Learned-multigrid form: every segment restarts the inner CG from the true
+// residual (r32 = scale r64, d = 0, p_old = 0, q = 0, first-step flag),
+// stopping it once |r32| has dropped by inner_rtol or the target is met.
+__global__ void k_dc_prepare_mg(const Grid g, int px, long long vol, const double* __restrict__ r64,
+                                const uint8_t* __restrict__ nodemask, float* __restrict__ p32b,
+                                float* __restrict__ r32, float* __restrict__ d32,
+                                float* __restrict__ q32, const Reducer red, SolverScalars* ss,
+                                DcCtl* ctl, cudaGraphConditionalHandle inner) {
+    __shared__ double sh[32];
+    __shared__ double out[1];
+    const double scale = ctl->scale;
+    double rrd = 0.0;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < g.nnode;
+         n += (long long)gridDim.x * blockDim.x) {
+        const long long pp = (n % g.nx) + (long long)px * (n / g.nx);
+        const uint8_t m = nodemask[n];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long d = c * vol + pp;
+            const float rv = ((m >> c) & 1) ? 0.f : (float)(r64[3 * n + c] * scale);
+            r32[d] = rv;
+            d32[d] = 0.f;
+            p32b[d] = 0.f;
+            q32[d] = 0.f;
+            rrd += (double)(rv * rv);
+        }
+    }
+    double v[1] = {rrd};
+    if (grid_sum<1>(red, v, sh, out) && threadIdx.x == 0) {
+        const double rr = out[0];
+        ss->beta = 0.0;
+        ss->zcoef = 1.0;
+        ss->pad0 = 1;
+        ss->tol2 = fmax(ctl->delta2 * rr, ctl->target2);
+        ss->rr = rr;
+        ss->it = 0;
+        ss->done = 0;
+        if (!isfinite(rr)) {
+            ss->status = TO3D_ENUMERIC;
+            ss->done = 1;
+        } else if (rr <= ss->tol2) {
+            ss->done = 1;
+        }
+        cudaGraphSetConditional(inner, ss->done ? 0u : 1u);
+    }
+}
+
 __global__ void k_inner_cond(const SolverScalars* ss, DcCtl* ctl, cudaGraphConditionalHandle inner) {
     const bool more = !ss->done && ++ctl->guard < kGuardChunks;
     cudaGraphSetConditional(inner, more ? 1u : 0u);
@@ -224,8 +271,10 @@ static cudaError_t build_iter_graph(to3d_ctx* c) {
         launch_filter(c, s0, 1, c->x, nullptr, c->xphys);
         launch_pin_passive(c, s0, c->xphys);
     }
+    const bool lmg = c->prm.precond == TO3D_LMG;
     launch_simp(c, s0, xa);
     launch_diag(c, s0, c->E);
+    if (lmg) mg_setup_launch(c, s0);
     launch_matvec64(c, s0, c->E, c->u, c->q, false);
     launch_residual64(c, s0, c->f, c->q, c->r, true);
     cudaGraphConditionalHandle h_outer, h_inner, h_oc;
@@ -234,10 +283,19 @@ static cudaError_t build_iter_graph(to3d_ctx* c) {
     CE(begin_while(s0, s1, h_outer));
     {
         CE(new_handle(s1, &h_inner, 0));
-        k_dc_prepare<<<152 * 4, 256, 0, s1>>>(g, c->px, c->vol, c->r, c->dinv32, c->p32a, c->p32b,
-                                              c->r32, c->d32, c->red, c->ss, ctl, h_inner);
+        if (lmg)
+            k_dc_prepare_mg<<<152 * 4, 256, 0, s1>>>(g, c->px, c->vol, c->r, c->nodemask, c->p32b,
+                                                     c->r32, c->d32, c->q32, c->red, c->ss, ctl,
+                                                     h_inner);
+        else
+            k_dc_prepare<<<152 * 4, 256, 0, s1>>>(g, c->px, c->vol, c->r, c->dinv32, c->p32a,
+                                                  c->p32b, c->r32, c->d32, c->red, c->ss, ctl,
+                                                  h_inner);
         CE(begin_while(s1, s2, h_inner));
-        for (int i = 0; i < kInnerChunk; ++i) launch_pcg32_iter(c, s2, prec, i & 1);
+        for (int i = 0; i < kInnerChunk; ++i) {
+            if (lmg) mg_pcg_iter_launch(c, s2, prec, i & 1);
+            else launch_pcg32_iter(c, s2, prec, i & 1);
+        }
         k_inner_cond<<<1, 1, 0, s2>>>(c->ss, ctl, h_inner);
         CE(end_while(s2));
         k_axpy_ctl<<<152 * 4, 256, 0, s1>>>(g, c->px, c->vol, c->u, c->d32, ctl);
@@ -390,7 +448,9 @@ to3d_status to3d_batch_create(int32_t nprob, const to3d_params* params, const ui
             cudaMemcpy(c->dcctl, &h, sizeof(DcCtl), cudaMemcpyHostToDevice) != cudaSuccess ||
             (c->prm.filter == TO3D_FILTER_DENS &&
              cudaMalloc(&c->xphys, sizeof(double) * c->g.nel) != cudaSuccess) ||
-            autotune_tc(c) != cudaSuccess || build_iter_graph(c) != cudaSuccess) {
+            autotune_tc(c) != cudaSuccess ||
+            (c->prm.precond == TO3D_LMG && mg_capture_ready(c) != TO3D_OK) ||
+            build_iter_graph(c) != cudaSuccess) {
             batch_free(b);
             return TO3D_ECUDA;
         }
@@ -400,6 +460,21 @@ to3d_status to3d_batch_create(int32_t nprob, const to3d_params* params, const ui
         return TO3D_ECUDA;
     }
     *out = b;
+    return TO3D_OK;
+}
+
+to3d_status to3d_batch_set_mg_params(to3d_batch* b, const double* theta, int64_t n) {
+    if (!b || !theta) return TO3D_EINVAL;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return TO3D_ECUDA;
+    for (to3d_ctx* c : b->ctx) {
+        if (c->prm.precond != TO3D_LMG) return TO3D_ESTATE;
+        to3d_status st = to3d_mg_set_params(c, theta, n);
+        if (st != TO3D_OK) return st;
+        // the parameters are kernel arguments of the captured set-up: capture again
+        if (c->g_iter) cudaGraphExecDestroy(c->g_iter);
+        c->g_iter = nullptr;
+        if (build_iter_graph(c) != cudaSuccess) return TO3D_ECUDA;
+    }
     return TO3D_OK;
 }
 

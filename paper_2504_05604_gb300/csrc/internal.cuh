@@ -246,6 +246,9 @@ void mg_operator_changed(to3d_ctx* c);
 to3d_status mg_apply64(to3d_ctx* c, const double* r, double* z, double rnorm);
 to3d_status mg_fcg_io(to3d_ctx* c, FcgIO* io);
 to3d_status solve_dc_mg(to3d_ctx* c, const double* f, double fnorm, to3d_solve_info* info);
+to3d_status mg_capture_ready(to3d_ctx* c);
+void mg_setup_launch(to3d_ctx* c, cudaStream_t s);
+void mg_pcg_iter_launch(to3d_ctx* c, cudaStream_t s, int prec, int parity);
 constexpr int kElementThreads = 256;   // threads per block of the element kernels
 void launch_filter(to3d_ctx* c, cudaStream_t s, int mode, const double* a, const double* b,
                    double* out);

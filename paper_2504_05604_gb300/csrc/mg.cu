@@ -619,9 +619,10 @@ static to3d_status ensure_mg(to3d_ctx* c) {
 
 // Coarse moduli, diagonals and smoothing weights for the fine moduli c->E
 // (c->dinv32 must already belong to them).
-static to3d_status setup_levels(to3d_ctx* c) {
+// The set-up's launches on stream s (capturable: the batched engine puts
+// them into its per-problem OC-iteration graph).
+static void setup_levels_on(to3d_ctx* c, cudaStream_t s) {
     Mg* m = mg_of(c);
-    cudaStream_t s = c->stream;
     for (size_t l = 1; l < m->lv.size(); ++l) {
         to3d_ctx* f = m->lv[l - 1].ctx;
         to3d_ctx* k = m->lv[l].ctx;
@@ -645,6 +646,11 @@ static to3d_status setup_levels(to3d_ctx* c) {
         k_pow_final<<<1, 1, 0, s>>>(out, w_of(m, (int)l), kPowerMargin, m->l1, m->wdev, (int)l, m->lamdev);
         c->launches += 2 + 3 * kPowerSteps;
     }
+}
+
+static to3d_status setup_levels(to3d_ctx* c) {
+    Mg* m = mg_of(c);
+    setup_levels_on(c, c->stream);
     m->params_dirty = false;
     return launch_check(c, "multigrid set-up");
 }
@@ -861,6 +867,13 @@ to3d_status solve_dc_mg(to3d_ctx* c, const double* f, double fnorm, to3d_solve_i
     return TO3D_OK;
 }
 
+// Pieces for the batched engine's captured OC-iteration graph.
+to3d_status mg_capture_ready(to3d_ctx* c) { return ensure_mg(c); }
+void mg_setup_launch(to3d_ctx* c, cudaStream_t s) { setup_levels_on(c, s); }
+void mg_pcg_iter_launch(to3d_ctx* c, cudaStream_t s, int prec, int parity) {
+    mgpcg_iter(c, mg_of(c), s, prec, parity);
+}
+
 // Buffers and preconditioner of flexible CG with the cycle.
 static to3d_status mg_apply_fcg(to3d_ctx* c, const double* r, double* z, double rr) {
     return mg_apply64(c, r, z, std::sqrt(rr));
@@ -962,6 +975,10 @@ to3d_status to3d_mg_set_params(to3d_ctx* c, const double* theta, int64_t n) {
     m->params_dirty = true;
     m->trained = true;
     return TO3D_OK;
+}
+
+to3d_status mg_set_params_ctx(to3d_ctx* c, const double* theta, int64_t n) {
+    return to3d_mg_set_params(c, theta, n);
 }
 
 to3d_status to3d_mg_levels(to3d_ctx* c, int32_t* nlev) {

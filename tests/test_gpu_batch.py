@@ -97,3 +97,36 @@ def test_batch_density_filter_matches_oracle_loop():
             assert r["halvings"] == h.halvings
         assert np.abs(batch.density(i) - x_ref).max() <= 1e-4
     batch.close()
+
+
+def test_batch_with_learned_multigrid_matches_oracle_loop():
+    """The learned-multigrid defect correction inside the per-problem graphs
+    (set-up, V-cycles and MG-PCG captured with the device-side loops), with
+    non-default parameters set after creation."""
+    from paper_2504_05604_gb300 import LMG, Batch
+    probs = small_batch()
+    iters = 4
+    batch = Batch(probs, precision=1, precond=LMG, inner_rtol=0.01)
+    batch.set_mg_params([0.8, 0.8, 0.8, 0.8, 0.7, 0.9, 0.7, 1.8, 1.8, 1.6])
+    recs = [batch.step() for _ in range(iters)]
+    for i, prob in enumerate(probs):
+        x_ref, hist = topopt.top3d(prob, iters=iters, solver="direct")
+        for it in range(iters):
+            r, h = recs[it][i], hist[it]
+            assert r["status"] == 0 and r["relres"] <= 1e-8
+            assert r["compliance"] == pytest.approx(h.compliance, rel=1e-5)
+            assert r["halvings"] == h.halvings
+        assert np.abs(batch.density(i) - x_ref).max() <= 1e-4
+    batch.close()
+
+
+def test_full_synthetic_batch_with_learned_multigrid():
+    from paper_2504_05604_gb300 import LMG, Batch
+    probs = problems.config_batched(64)
+    batch = Batch(probs, precision=1, precond=LMG, inner_rtol=0.01)
+    for _ in range(2):
+        recs = batch.step()
+    for i, prob in enumerate(probs):
+        assert recs[i]["status"] == 0 and recs[i]["relres"] <= 1e-8
+        assert abs(recs[i]["volume"] - prob.volfrac) < 2e-3
+    batch.close()
