@@ -159,6 +159,18 @@ def config_paper_benchmark(iters: int = 200) -> Problem:
                       rmin=4.0, iters=iters, name="cantilever 32x16x16 (paper benchmark)")
 
 
+def config_paper_usage(iters: int = 200) -> Problem:
+    """The paper's usage example (Section 3): the 32x16x16 benchmark
+    cantilever with a cylindrical non-design obstacle.  The paper does not
+    give the obstacle's geometry; here: a void cylinder along z through the
+    whole depth, axis at (x, y) = (16, 8) (mid-span, mid-height), radius 3.5
+    elements."""
+    pas = void_cylinder_z(32, 16, 16, 16.0, 8.0, 3.5)
+    return cantilever(32, 16, 16, load="node", load_node=(32, 0, 8), volfrac=0.2,
+                      rmin=4.0, iters=iters, passive=pas,
+                      name="cantilever 32x16x16 with a cylindrical obstacle (paper usage example)")
+
+
 def config_batched(nprob: int = 64, seed: int = 20250407) -> List[Problem]:
     """Independent cantilevers of uneven sizes with 0-3 spherical voids."""
     rng = np.random.Generator(np.random.PCG64(seed))
