@@ -108,7 +108,11 @@ typedef struct {
                           * accuracy; needs a nu whose lambda / mu is a small
                           * rational, else the CUDA-core FP64 kernel runs);
                           * 0 (default): the CUDA-core FP64 kernel            */
-    int32_t reserved[3];
+    int32_t mg_keep_dir; /* TO3D_LMG with a *_DC precision: 1 keeps the inner
+                          * CG's direction across FP64 residual replacements
+                          * (Fletcher-Reeves beta right after one), 0 restarts
+                          * it at each replacement                            */
+    int32_t reserved[2];
 } to3d_params;
 
 typedef struct {

@@ -298,8 +298,12 @@ __global__ void k_pcg_dots(long long vol, const float* __restrict__ r, const flo
     if (grid_sum<2>(red, v, sh, out) && threadIdx.x == 0) {
         const double rzn = out[0];
         const bool first = ss->pad0 != 0;
-        const double beta = first ? 0.0 : -ss->alpha * out[1] / ss->rz;
+        // right after a residual replacement the recurrence r_new - r_old =
+        // -alpha q_old no longer holds: Fletcher-Reeves beta once
+        const bool fr = ss->pad1 != 0;
+        const double beta = first ? 0.0 : (fr ? rzn / ss->rz : -ss->alpha * out[1] / ss->rz);
         ss->pad0 = 0;
+        ss->pad1 = 0;
         ss->beta = beta;
         ss->zcoef = 1.0;
         ss->rz = rzn;
@@ -491,6 +495,44 @@ __global__ void __launch_bounds__(kCoarseThreads)
         const long long p = i + (long long)px * jk;
 #pragma unroll
         for (int c = 0; c < 3; ++c) z[c * vol + p] = zs[3 * n + c];
+    }
+}
+
+// Residual replacement that keeps the inner CG's direction: r32 = scale r64
+// (masked), d = 0; |r32|^2 against the next segment's target; the next
+// beta is Fletcher-Reeves.
+__global__ void k_pcg_replace(const Grid g, int px, long long vol, const double* __restrict__ r64,
+                              double scale, const uint8_t* __restrict__ nodemask, float* __restrict__ r32,
+                              float* __restrict__ d32, const Reducer red, SolverScalars* ss, double delta2,
+                              double target2) {
+    __shared__ double sh[32];
+    __shared__ double out[1];
+    double rr = 0.0;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < g.nnode;
+         n += (long long)gridDim.x * blockDim.x) {
+        const long long p = (n % g.nx) + (long long)px * (n / g.nx);
+        const uint8_t m = nodemask[n];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float v = ((m >> c) & 1) ? 0.f : (float)(r64[3 * n + c] * scale);
+            r32[c * vol + p] = v;
+            d32[c * vol + p] = 0.f;
+            rr = fma((double)v, (double)v, rr);
+        }
+    }
+    double v[1] = {rr};
+    if (grid_sum<1>(red, v, sh, out) && threadIdx.x == 0) {
+        ss->rr = out[0];
+        ss->pad1 = 1;
+        ss->it = 0;
+        ss->done = 0;
+        ss->tol2 = fmax(delta2 * out[0], target2);
+        if (!isfinite(out[0])) {
+            ss->status = TO3D_ENUMERIC;
+            ss->done = 1;
+        } else if (out[0] <= ss->tol2) {
+            ss->done = 1;
+        }
     }
 }
 
@@ -818,14 +860,33 @@ to3d_status solve_dc_mg(to3d_ctx* c, const double* f, double fnorm, to3d_solve_i
     int total = 0, outer = 0, status = TO3D_OK, stalls = 0;
     double relres = 0.0;
     if ((st = true_residual64(c, f, fnorm, &relres))) return st;
+    // keep: one inner CG across the replacements (scale fixed by the first
+    // residual); else each segment restarts at unit RMS
+    const bool keep = c->prm.mg_keep_dir != 0;
+    double scale = 0.0;
+    bool restart = true;
+    int last_its = 0;
     while (relres > tol && fnorm > 0.0) {
         const double rnorm = relres * fnorm;
-        const double scale = std::sqrt((double)ndof) / rnorm;
+        if (!keep || scale == 0.0) scale = std::sqrt((double)ndof) / rnorm;
         const double t = 0.5 * tol * fnorm * scale;
-        launch_ss_reset(c, c->stream, std::fmax(delta * delta * (double)ndof, t * t),
-                        c->prm.cg_maxit - total);
-        k_pcg_init<<<nblocks(c->g.nnode), kThreads, 0, c->stream>>>(
-            c->g, c->px, c->vol, c->r, scale, c->nodemask, c->r32, c->d32, c->p32b, c->q32, c->red, c->ss);
+        if (restart) {
+            launch_ss_reset(c, c->stream, std::fmax(delta * delta * (double)ndof, t * t),
+                            c->prm.cg_maxit - total);
+            k_pcg_init<<<nblocks(c->g.nnode), kThreads, 0, c->stream>>>(
+                c->g, c->px, c->vol, c->r, scale, c->nodemask, c->r32, c->d32, c->p32b, c->q32, c->red,
+                c->ss);
+        } else {
+            // the captured chunks take p_old from p32b first: after an odd
+            // number of iterations the last direction sits in p32a
+            if (last_its & 1)
+                MG_CK(cudaMemcpyAsync(c->p32b, c->p32a, sizeof(float) * 3 * c->vol,
+                                      cudaMemcpyDeviceToDevice, c->stream));
+            launch_ss_segment(c, c->stream, t * t, c->prm.cg_maxit - total);
+            k_pcg_replace<<<nblocks(c->g.nnode), kThreads, 0, c->stream>>>(
+                c->g, c->px, c->vol, c->r, scale, c->nodemask, c->r32, c->d32, c->red, c->ss,
+                delta * delta, t * t);
+        }
         c->launches++;
         int it0 = 0;
         for (;;) {
@@ -837,6 +898,7 @@ to3d_status solve_dc_mg(to3d_ctx* c, const double* f, double fnorm, to3d_solve_i
         }
         const int its = c->ss_h->it;
         total += its;
+        last_its = its;
         if (c->ss_h->status == TO3D_ETIMEOUT || c->ss_h->status == TO3D_ENUMERIC) {
             status = c->ss_h->status;
             break;
@@ -844,6 +906,10 @@ to3d_status solve_dc_mg(to3d_ctx* c, const double* f, double fnorm, to3d_solve_i
         launch_axpy_d32(c, c->stream, 1.0 / scale);
         const double prev = relres;
         if ((st = true_residual64(c, f, fnorm, &relres))) return st;
+        // keep the direction unless the true residual failed to halve (the
+        // recurrence ran away from it): then restart from it
+        restart = !keep || relres > 0.5 * prev;
+        if (restart) scale = 0.0;
         if (c->trace)
             std::fprintf(stderr, "to3d: mg segment %d: %d inner its (total %d), relres %.3e -> %.3e\n",
                          outer, its, total, prev, relres);
