@@ -228,18 +228,33 @@ __global__ void k_coarsen(const Grid gf, const double* __restrict__ Ef, const Gr
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= gc.nel) return;
     const int i = e % gc.nelx, j = (e / gc.nelx) % gc.nely, k = e / ((long long)gc.nelx * gc.nely);
-    double acc = 0.0;
+    // powers in FP32 (the coarse operator needs no more than that) of the
+    // children relative to the largest one, so that no power underflows:
+    // (mean E^q)^(1/q) = E_max (mean (E / E_max)^q)^(1/q)
+    double ch[8];
+    double vmax = 0.0;
     for (int c = 0; c < 2; ++c)
         for (int b = 0; b < 2; ++b)
             for (int a = 0; a < 2; ++a) {
                 const int fi = 2 * i + a, fj = 2 * j + b, fk = 2 * k + c;
-                if (fi < gf.nelx && fj < gf.nely && fk < gf.nelz) {
-                    const double v = Ef[elem_id(gf, fi, fj, fk)];
-                    acc += (q == 1.0) ? v : pow(v, q);
-                }
+                const double v = (fi < gf.nelx && fj < gf.nely && fk < gf.nelz)
+                                     ? Ef[elem_id(gf, fi, fj, fk)] : 0.0;
+                ch[a + 2 * b + 4 * c] = v;
+                vmax = fmax(vmax, v);
             }
-    const double m = acc / 8.0;
-    const double v = s * ((q == 1.0) ? m : pow(m, 1.0 / q));
+    double v = 0.0;
+    if (vmax > 0.0) {
+        if (q == 1.0) {
+            double acc = 0.0;
+            for (int t = 0; t < 8; ++t) acc += ch[t];
+            v = s * acc / 8.0;
+        } else {
+            const float qf = (float)q;
+            float acc = 0.f;
+            for (int t = 0; t < 8; ++t) acc += powf((float)(ch[t] / vmax), qf);
+            v = s * vmax * (double)powf(acc / 8.f, 1.f / qf);
+        }
+    }
     Ec[e] = v;
     E32c[i + (long long)pexc * (j + (long long)gc.nely * k)] = (float)v;
 }
@@ -377,19 +392,25 @@ __global__ void k_pow_dots(long long vol, const float* __restrict__ z, const flo
                            const Reducer red, double* out_dev) {
     __shared__ double sh[64];
     __shared__ double o2[2];
+    // FP32 products and per-node partial sums (a Rayleigh quotient needs no
+    // more), FP64 across nodes, blocks and the grid
     double a = 0.0, b = 0.0;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < vol;
          n += (long long)gridDim.x * blockDim.x) {
         const float di = dinv[n];
         const uint8_t m = maskp[n];
         if (!(di > 0.f)) continue;
+        const float dn = 1.f / di;
+        float pa = 0.f, pb = 0.f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             if ((m >> c) & 1) continue;
-            const double zv = z[c * vol + n];
-            a = fma(zv, (double)t[c * vol + n], a);
-            b = fma(zv, zv / (double)di, b);
+            const float zv = z[c * vol + n];
+            pa = fmaf(zv, t[c * vol + n], pa);
+            pb = fmaf(zv * zv, dn, pb);
         }
+        a += (double)pa;
+        b += (double)pb;
     }
     double v[2] = {a, b};
     if (grid_sum<2>(red, v, sh, o2) && threadIdx.x == 0) {
