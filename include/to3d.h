@@ -112,7 +112,9 @@ typedef struct {
                           * CG's direction across FP64 residual replacements
                           * (Fletcher-Reeves beta right after one), 0 restarts
                           * it at each replacement                            */
-    int32_t reserved[2];
+    int32_t mg_nu;       /* TO3D_LMG: damped-Jacobi sweeps before and after
+                          * each coarse correction (0: 1)                     */
+    int32_t reserved[1];
 } to3d_params;
 
 typedef struct {

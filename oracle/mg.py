@@ -26,8 +26,8 @@ weights prod_d (1 - |F_d - 2 C_d| / 2) for |F_d - 2 C_d| <= 1, clamped dofs
 of either grid zeroed; restriction is its transpose.
 
 Smoother.  Damped Jacobi, z <- z + om_l D^-1 (b - K z), D = diag(K) per dof
-(0 on clamped dofs), one sweep before and one after the coarse correction,
-the first from z = 0.  On the coarsest level, `sweeps` sweeps from z = 0.
+(0 on clamped dofs), nu sweeps (default 1) before and nu after the coarse
+correction, the first from z = 0.  On the coarsest level, `sweeps` sweeps from z = 0.
 The damping is relative to the level's largest eigenvalue of D^-1 K:
 om_l = w_l * 2 / lam_l with lam_l = min(1.2 rq, l1), rq the Rayleigh
 quotient z^T K z / z^T D z after POWER_STEPS steps of the power iteration
@@ -178,8 +178,9 @@ def damping(L: Level, w):
     return w * 2.0 / L.lam
 
 
-def vcycle(lv: List[Level], KE, b, w, sweeps, l=0):
-    """z = V b on level l (recursive)."""
+def vcycle(lv: List[Level], KE, b, w, sweeps, l=0, nu=1):
+    """z = V b on level l (recursive); nu damped-Jacobi sweeps before and
+    after each coarse correction."""
     L = lv[l]
     om = damping(L, w[l])
     z = om * L.dinv * b
@@ -187,9 +188,13 @@ def vcycle(lv: List[Level], KE, b, w, sweeps, l=0):
         for _ in range(sweeps - 1):
             z = z + om * L.dinv * (b - operator(L, KE, z))
         return z
+    for _ in range(nu - 1):
+        z = z + om * L.dinv * (b - operator(L, KE, z))
     bc = restrict(L, lv[l + 1], b - operator(L, KE, z))
-    z = z + prolong(L, lv[l + 1], vcycle(lv, KE, bc, w, sweeps, l + 1))
-    return z + om * L.dinv * (b - operator(L, KE, z))
+    z = z + prolong(L, lv[l + 1], vcycle(lv, KE, bc, w, sweeps, l + 1, nu))
+    for _ in range(nu):
+        z = z + om * L.dinv * (b - operator(L, KE, z))
+    return z
 
 
 def energy_loss(K, r, e, z):

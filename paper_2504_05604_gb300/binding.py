@@ -36,7 +36,7 @@ class Params(C.Structure):
                 ("cg_maxit", C.c_int32), ("filter", C.c_int32), ("precision", C.c_int32),
                 ("precond", C.c_int32), ("oc_levels", C.c_int32), ("warm_start", C.c_int32),
                 ("fcg_ref_iters", C.c_int32), ("mg_sweeps", C.c_int32), ("fp64_tc", C.c_int32),
-                ("mg_keep_dir", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("mg_keep_dir", C.c_int32), ("mg_nu", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 class IterInfo(C.Structure):

@@ -578,7 +578,8 @@ to3d_status to3d_create(const to3d_params* prm, const uint8_t* fixed, const doub
         return TO3D_EINVAL;
     if (prm->precond != TO3D_JACOBI && prm->precond != TO3D_CNN_FCG && prm->precond != TO3D_LMG)
         return TO3D_EINVAL;
-    if (prm->mg_sweeps < 0 || prm->mg_sweeps > 1000) return TO3D_EINVAL;
+    if (prm->mg_sweeps < 0 || prm->mg_sweeps > 1000 || prm->mg_nu < 0 || prm->mg_nu > 8)
+        return TO3D_EINVAL;
     {
         // a NaN or Inf load would make every residual test false and end the
         // solves "converged": reject it here

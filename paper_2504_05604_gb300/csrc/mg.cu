@@ -79,6 +79,7 @@ struct Mg {
     double* lamdev = nullptr;         // eigenvalue bound per level (device)
     double l1 = 59.0 / 11.0;          // max_a sum_b |KE_ab| / KE_aa
     int sweeps = 6;
+    int nu = 1;                       // smoothing sweeps before and after the coarse correction
     int prec = TO3D_BF16_DC;
     cudaGraphExec_t cycle = nullptr;  // ctx->r32 -> lv[0].z, captured
     long long cycle_launches = 0;     // kernels in one cycle
@@ -599,6 +600,7 @@ static to3d_status ensure_mg(to3d_ctx* c) {
     c->mg = m;
     default_theta(m->theta);
     m->sweeps = c->prm.mg_sweeps > 0 ? c->prm.mg_sweeps : 6;
+    m->nu = c->prm.mg_nu > 0 ? c->prm.mg_nu : 1;
     m->prec = c->prm.precision == TO3D_F64 ? TO3D_BF16_DC : c->prm.precision;
     // clamp masks on the host, level by level
     const Grid& g0 = c->g;
@@ -748,6 +750,13 @@ static void cycle_launch(to3d_ctx* c, Mg* m, cudaStream_t s, size_t l, const flo
     }
     Level& C = m->lv[l + 1];
     to3d_ctx* kc = C.ctx;
+    auto sweep = [&]() {
+        op();
+        k_jacobi<<<nblocks(vol), kThreads, 0, s>>>(vol, b, L.t, k->dinv32, k->maskp, m->wdev, (int)l,
+                                                  L.z, ss);
+        c->launches++;
+    };
+    for (int i = 1; i < m->nu; ++i) sweep();     // further pre-smoothing sweeps
     op();
     k_restrict<<<dim3((kc->g.nx + 63) / 64, kc->g.ny, kc->g.nz), 64, 0, s>>>(
         k->g, k->px, vol, b, L.t, k->maskp, kc->g, kc->px, kc->vol, kc->maskp, kc->r32, ss);
@@ -756,9 +765,7 @@ static void cycle_launch(to3d_ctx* c, Mg* m, cudaStream_t s, size_t l, const flo
     k_prolong<<<dim3((k->g.nx + 127) / 128, k->g.ny, k->g.nz), 128, 0, s>>>(
         k->g, k->px, vol, k->maskp, L.z, kc->g, kc->px, kc->vol, C.z, ss);
     c->launches++;
-    op();
-    k_jacobi<<<nblocks(vol), kThreads, 0, s>>>(vol, b, L.t, k->dinv32, k->maskp, m->wdev, (int)l, L.z, ss);
-    c->launches++;
+    for (int i = 0; i < m->nu; ++i) sweep();     // post-smoothing
 }
 
 // Make sure the hierarchy belongs to the current fine operator.

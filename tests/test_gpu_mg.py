@@ -26,13 +26,13 @@ def per_level(theta, nlev):
     return w, q, s
 
 
-def oracle_cycle(prob, x, r, theta, sweeps=6):
+def oracle_cycle(prob, x, r, theta, sweeps=6, nu=1):
     KE = fem.element_stiffness(prob.nu)
     E = fem.simp_modulus(x, prob.penal, prob.E0, prob.Emin)
     lv = mg.hierarchy(prob.nelx, prob.nely, prob.nelz, prob.fixed)
     w, q, s = per_level(theta, len(lv))
     mg.setup(lv, E, KE, q, s)
-    return mg.vcycle(lv, KE, np.where(prob.fixed != 0, 0.0, r), w, sweeps), len(lv)
+    return mg.vcycle(lv, KE, np.where(prob.fixed != 0, 0.0, r), w, sweeps, nu=nu), len(lv)
 
 
 @pytest.mark.parametrize("dims,prec,tol", [((20, 8, 6), 2, 2e-4), ((20, 8, 6), 1, 3e-2),
@@ -58,6 +58,18 @@ def test_cycle_matches_oracle(dims, prec, tol):
     zr2, _ = oracle_cycle(prob, x, r, th2)
     err2 = np.linalg.norm(z2 - zr2) / np.linalg.norm(zr2)
     assert err2 <= tol, err2
+    ctx.close()
+
+
+def test_cycle_with_two_smoothing_sweeps_matches_oracle():
+    from paper_2504_05604_gb300 import LMG
+    prob = random_problem(20, 8, 6, seed=34)
+    x = problems.random_density(prob.nel, 3, 1e-3, 1.0)
+    r = problems.random_vector(prob.ndof, 4)
+    ctx = lib_ctx(prob, precision=2, precond=LMG, mg_nu=2, mg_sweeps=9)
+    z = ctx.mg_apply(x, r)
+    zr, _ = oracle_cycle(prob, x, r, ctx.mg_params(), sweeps=9, nu=2)
+    assert np.linalg.norm(z - zr) <= 2e-4 * np.linalg.norm(zr)
     ctx.close()
 
 
