@@ -69,7 +69,8 @@ def parse():
                     help="0 fp64, 1 bf16, 2 bf16 hi+lo, 3 fp16, 4 fp16 hi+lo (tensor-core forms "
                          "with FP64 defect correction)")
     ap.add_argument("--size", default="480x160x80")
-    ap.add_argument("--workload", default="large", choices=["large", "batched64", "paper32"],
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "batched64", "paper32", "config1", "config2"],
                     help="large: the 480x160x80 cantilever; batched64: 64 seeded uneven "
                          "cantilevers stepped together (extra measurement)")
     ap.add_argument("--precond", default="lmg", choices=["lmg", "jacobi"],
@@ -718,10 +719,54 @@ def paper_benchmark(args):
     }))
 
 
+def whole_runs(args):
+    """Whole runs of the 60x20x4 (50 OC iterations) or the 240x80x40
+    void-cylinder (100 OC iterations) cantilever: plain FP64 Jacobi-PCG, the
+    chosen form (learned parameters as for the large workload) and Jacobi
+    BF16 defect correction, each timed over the whole run."""
+    import torch
+    from paper_2504_05604_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2504_05604_gb300 import LMG, Context
+    from synth import problems
+    prob = problems.config_small() if args.workload == "config1" else problems.config_void_cylinder()
+    theta = train_lmg(torch.cuda.Stream())[0]
+    forms = {"fp64": dict(precision=0),
+             PREC_NAMES[args.precision] + "-lmg": dict(precision=args.precision, precond=LMG,
+                                                       inner_rtol=args.inner_rtol, fp64_tc=1),
+             "fp64-lmg (learned FCG)": dict(precision=0, precond=LMG, fp64_tc=1),
+             "bf16-dc (Jacobi)": dict(precision=1, inner_rtol=0.3)}
+    out = {}
+    for name, kw in forms.items():
+        ctx = Context.from_problem(prob, **kw)
+        if kw.get("precond") == LMG:
+            ctx.set_mg_params(theta)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        recs = ctx.run(prob.iters)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        out[name] = {"value": prob.iters / te, "unit": UNIT, "total_s": te,
+                     "final_compliance": recs[-1]["compliance"],
+                     "final_volume": recs[-1]["volume"],
+                     "cg_iters_mean": statistics.mean(r["cg_iters"] for r in recs),
+                     "cg_iters_max": max(r["cg_iters"] for r in recs),
+                     "status": max(r["status"] for r in recs)}
+        ctx.close()
+    ref = out["fp64"]["final_compliance"]
+    for v in out.values():
+        v["final_compliance_vs_fp64"] = v["final_compliance"] / ref - 1.0
+    print(json.dumps({"metric": f"OC iters/s, whole run of {prob.name} ({prob.iters} OC iterations)",
+                      "unit": UNIT, "forms": out}))
+
+
 def main():
     args = parse()
     if args.workload == "batched64" and not args.cpu_leg and args.impl == "ours":
         batched(args)
+        return
+    if args.workload in ("config1", "config2") and not args.cpu_leg and args.impl == "ours":
+        whole_runs(args)
         return
     if args.workload == "paper32" and not args.cpu_leg and args.impl == "ours":
         paper_benchmark(args)
