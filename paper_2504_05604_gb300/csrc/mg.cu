@@ -72,6 +72,30 @@ struct Snap {
     int design = 0;              // index into Mg::designs
 };
 
+constexpr int kBottomMaxLevels = 8;
+constexpr int kBottomThreads = 1024;
+constexpr int kBottomSmem = 200 * 1024;
+
+struct BottomLevel {
+    Grid g;
+    int px, pex;
+    long long vol;
+    const float* E32;
+    const float* dinv32;
+    const uint8_t* maskp;
+    int ob, oz, ot, od, oE;      // float offsets in shared memory
+    int om;                      // byte offset of the clamp bits
+};
+
+struct BottomArgs {
+    int nb, lb, sweeps, nu;
+    BottomLevel L[kBottomMaxLevels];
+    const float* b_in;           // right-hand side of level lb (padded SoA)
+    float* z_out;                // solution of level lb (padded SoA)
+    const float* KE;             // unit KE, FP32
+    const float* wdev;
+};
+
 struct Mg {
     std::vector<Level> lv;
     double theta[kParams];
@@ -80,6 +104,9 @@ struct Mg {
     double l1 = 59.0 / 11.0;          // max_a sum_b |KE_ab| / KE_aa
     int sweeps = 6;
     int nu = 1;                       // smoothing sweeps before and after the coarse correction
+    int lb = 1 << 30;                 // first level of the one-CTA bottom cycle
+    BottomArgs bottom;                // its level table (b_in, z_out set per launch)
+    int bottom_smem = 0;
     int prec = TO3D_BF16_DC;
     cudaGraphExec_t cycle = nullptr;  // ctx->r32 -> lv[0].z, captured
     long long cycle_launches = 0;     // kernels in one cycle
@@ -89,7 +116,7 @@ struct Mg {
     double* dots = nullptr;
     double* dots_h = nullptr;
     float* ones = nullptr;            // per-node scaling 1 (fused direction p = z + beta p)
-    float* ke32 = nullptr;            // unit KE in FP32 (coarsest-level sweeps)
+    float* ke32 = nullptr;            // unit KE in FP32 (the one-CTA bottom cycle)
     CUtensorMap tm_ones;
     cudaGraphExec_t pcg = nullptr;    // chunk of inner MG-PCG iterations
     int pcg_prec = -1, pcg_n = 0;
@@ -445,78 +472,174 @@ __global__ void k_pow_final(const double* __restrict__ out, double w, double mar
     lam_out[l] = lam_ok;
 }
 
-// The coarsest level's Jacobi sweeps in one CTA (grids of at most
-// kCoarseNodes nodes): b, D^-1, the clamp bits and z in shared memory, the
-// operator element by element in FP32 on the CUDA cores (24 x 24 products,
-// shared-memory atomics into the nodes).  Same sweeps as the per-kernel
-// form: z = w D^-1 b, then sweeps - 1 times z += w D^-1 (b - K z).
-constexpr int kCoarseNodes = 1024;
-constexpr int kCoarseThreads = 256;
-
-__global__ void __launch_bounds__(kCoarseThreads)
-    k_coarse_sweeps(const Grid g, int px, long long vol, int pex, const float* __restrict__ b,
-                    const float* __restrict__ E32, const float* __restrict__ dinv,
-                    const uint8_t* __restrict__ maskp, const float* __restrict__ KE,
-                    const float* __restrict__ wdev, int l, int sweeps, float* __restrict__ z,
-                    const SolverScalars* ss) {
+// The V-cycle over the bottom levels in one CTA.  Levels lb..L whose
+// vectors, damping, clamp bits and moduli fit in shared memory together
+// (kBottomSmem) run inside one kernel: every operator application element by
+// element in FP32 on the CUDA cores (24 x 24 products, shared-memory atomics
+// into the nodes), restriction, prolongation and the damped-Jacobi sweeps
+// as in the per-level kernels, __syncthreads between the steps.  On the
+// largest grids that is the last four levels, whose per-level launches were
+// bound by launch latency.
+__global__ void __launch_bounds__(kBottomThreads, 1)
+    k_cycle_bottom(const __grid_constant__ BottomArgs a, const SolverScalars* ss) {
     if (skip(ss)) return;
-    __shared__ float Ks[576];
-    __shared__ float zs[3 * kCoarseNodes], ts[3 * kCoarseNodes], bs[3 * kCoarseNodes];
-    __shared__ float ds[kCoarseNodes];
-    __shared__ uint8_t ms[kCoarseNodes];
-    const int nn = (int)g.nnode, tid = threadIdx.x;
-    const float w = wdev[l];
-    for (int i = tid; i < 576; i += blockDim.x) Ks[i] = KE[i];
-    for (int n = tid; n < nn; n += blockDim.x) {
-        const int i = n % g.nx, jk = n / g.nx;
-        const long long p = i + (long long)px * jk;
-        const uint8_t m = maskp[p];
-        const float d = w * dinv[p];
-        ds[n] = d;
-        ms[n] = m;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float bv = b[c * vol + p];
-            bs[3 * n + c] = bv;
-            zs[3 * n + c] = ((m >> c) & 1) ? 0.f : d * bv;
+    extern __shared__ float bsm[];
+    uint8_t* bytes = reinterpret_cast<uint8_t*>(bsm);
+    float* Ks = bsm;                                  // 576 floats at offset 0
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < 576; i += nt) Ks[i] = a.KE[i];
+    for (int li = 0; li < a.nb; ++li) {
+        const BottomLevel& L = a.L[li];
+        const float w = a.wdev[a.lb + li];
+        const int nn = (int)L.g.nnode;
+        for (int n = tid; n < nn; n += nt) {
+            const int i = n % L.g.nx, jk = n / L.g.nx;
+            const long long p = i + (long long)L.px * jk;
+            bsm[L.od + n] = w * L.dinv32[p];
+            bytes[L.om + n] = L.maskp[p];
+            if (li == 0)
+                for (int c = 0; c < 3; ++c) bsm[L.ob + 3 * n + c] = a.b_in[c * L.vol + p];
+        }
+        for (long long e = tid; e < L.g.nel; e += nt) {
+            const int ei = (int)(e % L.g.nelx), ej = (int)((e / L.g.nelx) % L.g.nely),
+                      ek = (int)(e / ((long long)L.g.nelx * L.g.nely));
+            bsm[L.oE + e] = L.E32[ei + (long long)L.pex * (ej + (long long)L.g.nely * ek)];
         }
     }
     __syncthreads();
-    for (int sw = 1; sw < sweeps; ++sw) {
-        for (int i = tid; i < 3 * nn; i += blockDim.x) ts[i] = 0.f;
+
+    // t = K z on level li
+    auto op = [&](int li) {
+        const BottomLevel& L = a.L[li];
+        const int nn = (int)L.g.nnode;
+        float* z = bsm + L.oz;
+        float* t = bsm + L.ot;
+        for (int i = tid; i < 3 * nn; i += nt) t[i] = 0.f;
         __syncthreads();
-        for (long long e = tid; e < g.nel; e += blockDim.x) {
-            const int ei = (int)(e % g.nelx), ej = (int)((e / g.nelx) % g.nely),
-                      ek = (int)(e / ((long long)g.nelx * g.nely));
+        for (long long e = tid; e < L.g.nel; e += nt) {
+            const int ei = (int)(e % L.g.nelx), ej = (int)((e / L.g.nelx) % L.g.nely),
+                      ek = (int)(e / ((long long)L.g.nelx * L.g.nely));
             int nd[8];
             float ze[24];
 #pragma unroll
-            for (int a = 0; a < 8; ++a) {
-                nd[a] = (ei + (a & 1)) + g.nx * ((ej + ((a >> 1) & 1)) + g.ny * (ek + (a >> 2)));
+            for (int q = 0; q < 8; ++q) {
+                nd[q] = (ei + (q & 1)) + L.g.nx * ((ej + ((q >> 1) & 1)) + L.g.ny * (ek + (q >> 2)));
 #pragma unroll
-                for (int c = 0; c < 3; ++c) ze[3 * a + c] = zs[3 * nd[a] + c];
+                for (int c = 0; c < 3; ++c) ze[3 * q + c] = z[3 * nd[q] + c];
             }
-            const float Ee = E32[ei + (long long)pex * (ej + (long long)g.nely * ek)];
+            const float Ee = bsm[L.oE + e];
 #pragma unroll 4
             for (int r = 0; r < 24; ++r) {
                 float acc = 0.f;
 #pragma unroll
                 for (int k = 0; k < 24; ++k) acc = fmaf(Ks[r * 24 + k], ze[k], acc);
-                atomicAdd(&ts[3 * nd[r / 3] + r % 3], Ee * acc);
+                atomicAdd(&t[3 * nd[r / 3] + r % 3], Ee * acc);
             }
         }
         __syncthreads();
-        for (int i = tid; i < 3 * nn; i += blockDim.x) {
+    };
+    // z = d b (first sweep from 0) or z += d (b - t)
+    auto smooth = [&](int li, bool first) {
+        const BottomLevel& L = a.L[li];
+        const int nn = (int)L.g.nnode;
+        const float* d = bsm + L.od;
+        const float* b = bsm + L.ob;
+        const float* t = bsm + L.ot;
+        float* z = bsm + L.oz;
+        for (int i = tid; i < 3 * nn; i += nt) {
             const int n = i / 3, c = i - 3 * n;
-            if (!((ms[n] >> c) & 1)) zs[i] = fmaf(ds[n], bs[i] - ts[i], zs[i]);
+            if ((bytes[L.om + n] >> c) & 1) z[i] = 0.f;
+            else z[i] = first ? d[n] * b[i] : fmaf(d[n], b[i] - t[i], z[i]);
         }
         __syncthreads();
-    }
-    for (int n = tid; n < nn; n += blockDim.x) {
-        const int i = n % g.nx, jk = n / g.nx;
-        const long long p = i + (long long)px * jk;
+    };
+    // b_{li+1} = R (b_li - t_li)
+    auto restrict_to = [&](int li) {
+        const BottomLevel& F = a.L[li];
+        const BottomLevel& C = a.L[li + 1];
+        const int nc = (int)C.g.nnode;
+        for (int n = tid; n < nc; n += nt) {
+            const int i = n % C.g.nx, j = (n / C.g.nx) % C.g.ny, k = n / (C.g.nx * C.g.ny);
+            float acc[3] = {0.f, 0.f, 0.f};
+            for (int dk = -1; dk <= 1; ++dk) {
+                const int fk = 2 * k + dk;
+                if (fk < 0 || fk >= F.g.nz) continue;
+                for (int dj = -1; dj <= 1; ++dj) {
+                    const int fj = 2 * j + dj;
+                    if (fj < 0 || fj >= F.g.ny) continue;
+                    for (int di = -1; di <= 1; ++di) {
+                        const int fi = 2 * i + di;
+                        if (fi < 0 || fi >= F.g.nx) continue;
+                        const float wt = (dk ? 0.5f : 1.f) * (dj ? 0.5f : 1.f) * (di ? 0.5f : 1.f);
+                        const int f = fi + F.g.nx * (fj + F.g.ny * fk);
+                        const uint8_t m = bytes[F.om + f];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) z[c * vol + p] = zs[3 * n + c];
+                        for (int c = 0; c < 3; ++c)
+                            if (!((m >> c) & 1))
+                                acc[c] = fmaf(wt, bsm[F.ob + 3 * f + c] - bsm[F.ot + 3 * f + c], acc[c]);
+                    }
+                }
+            }
+            const uint8_t mc = bytes[C.om + n];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) bsm[C.ob + 3 * n + c] = ((mc >> c) & 1) ? 0.f : acc[c];
+        }
+        __syncthreads();
+    };
+    // z_li += P z_{li+1}
+    auto prolong_from = [&](int li) {
+        const BottomLevel& F = a.L[li];
+        const BottomLevel& C = a.L[li + 1];
+        const int nf = (int)F.g.nnode;
+        for (int n = tid; n < nf; n += nt) {
+            const int i = n % F.g.nx, j = (n / F.g.nx) % F.g.ny, k = n / (F.g.nx * F.g.ny);
+            const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
+            const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
+            const float w = ((i & 1) ? 0.5f : 1.f) * ((j & 1) ? 0.5f : 1.f) * ((k & 1) ? 0.5f : 1.f);
+            float acc[3] = {0.f, 0.f, 0.f};
+            for (int aa = 0; aa < nk; ++aa)
+                for (int bb = 0; bb < nj; ++bb)
+                    for (int cc = 0; cc < ni; ++cc) {
+                        const int cn = (i0 + cc) + C.g.nx * ((j0 + bb) + C.g.ny * (k0 + aa));
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) acc[c] = fmaf(w, bsm[C.oz + 3 * cn + c], acc[c]);
+                    }
+            const uint8_t m = bytes[F.om + n];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                if (!((m >> c) & 1)) bsm[F.oz + 3 * n + c] += acc[c];
+        }
+        __syncthreads();
+    };
+
+    const int last = a.nb - 1;
+    for (int li = 0; li < last; ++li) {
+        smooth(li, true);
+        for (int s = 1; s < a.nu; ++s) {
+            op(li);
+            smooth(li, false);
+        }
+        op(li);
+        restrict_to(li);
+    }
+    smooth(last, true);
+    for (int s = 1; s < a.sweeps; ++s) {
+        op(last);
+        smooth(last, false);
+    }
+    for (int li = last - 1; li >= 0; --li) {
+        prolong_from(li);
+        for (int s = 0; s < a.nu; ++s) {
+            op(li);
+            smooth(li, false);
+        }
+    }
+    const BottomLevel& L0 = a.L[0];
+    for (int n = tid; n < (int)L0.g.nnode; n += nt) {
+        const int i = n % L0.g.nx, jk = n / L0.g.nx;
+        const long long p = i + (long long)L0.px * jk;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a.z_out[c * L0.vol + p] = bsm[L0.oz + 3 * n + c];
     }
 }
 
@@ -652,6 +775,54 @@ static to3d_status ensure_mg(to3d_ctx* c) {
         MG_CK(cudaMemset(L.t, 0, bytes));
         if (!encode_vec_map(L.ctx, &L.tm_z, L.z, 3)) return set_err(c, TO3D_ECUDA, "multigrid TMA map");
     }
+    // the bottom levels that fit in one CTA's shared memory together
+    {
+        const int L = (int)m->lv.size();
+        long long used = 576 * 4;
+        int lb = L;
+        for (int l = L - 1; l >= 0 && L - l <= kBottomMaxLevels; --l) {
+            const Grid& g = m->lv[l].ctx->g;
+            const long long need = 4 * (10 * g.nnode + g.nel) + g.nnode + 16;
+            if (used + need > kBottomSmem) break;
+            used += need;
+            lb = l;
+        }
+        if (lb < L) {
+            BottomArgs& ba = m->bottom;
+            std::memset(&ba, 0, sizeof(ba));
+            ba.nb = L - lb;
+            ba.lb = lb;
+            ba.sweeps = m->sweeps;
+            ba.nu = m->nu;
+            int off = 576;
+            for (int i = 0; i < ba.nb; ++i) {
+                to3d_ctx* k = m->lv[lb + i].ctx;
+                BottomLevel& B = ba.L[i];
+                B.g = k->g;
+                B.px = k->px;
+                B.pex = k->pex;
+                B.vol = k->vol;
+                B.E32 = k->E32;
+                B.dinv32 = k->dinv32;
+                B.maskp = k->maskp;
+                const int n = (int)k->g.nnode;
+                B.ob = off; off += 3 * n;
+                B.oz = off; off += 3 * n;
+                B.ot = off; off += 3 * n;
+                B.od = off; off += n;
+                B.oE = off; off += (int)k->g.nel;
+            }
+            int boff = 4 * off;
+            for (int i = 0; i < ba.nb; ++i) {
+                ba.L[i].om = boff;
+                boff += (int)ba.L[i].g.nnode;
+            }
+            m->bottom_smem = (boff + 15) & ~15;
+            m->lb = lb;
+            MG_CK(cudaFuncSetAttribute(k_cycle_bottom, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kBottomSmem));
+        }
+    }
     const long long ndof = 3 * g0.nnode;
     MG_CK(cudaMalloc(&m->wdev, sizeof(float) * kMaxLevels));
     MG_CK(cudaMalloc(&m->lamdev, sizeof(double) * kMaxLevels));
@@ -660,6 +831,8 @@ static to3d_status ensure_mg(to3d_ctx* c) {
         for (int i = 0; i < 576; ++i) ke[i] = (float)c->ke.v[i];
         MG_CK(cudaMalloc(&m->ke32, sizeof(ke)));
         MG_CK(cudaMemcpy(m->ke32, ke, sizeof(ke), cudaMemcpyHostToDevice));
+        m->bottom.KE = m->ke32;
+        m->bottom.wdev = m->wdev;
     }
     {
         double l1 = 0.0;
@@ -730,10 +903,12 @@ static void cycle_launch(to3d_ctx* c, Mg* m, cudaStream_t s, size_t l, const flo
         launch_matvec_tc_io(k, s, m->prec, false, k->tm_r, L.tm_z, k->tm_d, nullptr, L.t, ss);
         if (k != c) c->launches++;
     };
-    if (l + 1 == m->lv.size() && k->g.nnode <= kCoarseNodes) {
-        k_coarse_sweeps<<<1, kCoarseThreads, 0, s>>>(k->g, k->px, vol, k->pex, b, k->E32, k->dinv32,
-                                                     k->maskp, m->ke32, m->wdev, (int)l, m->sweeps,
-                                                     L.z, ss);
+    if ((int)l == m->lb) {
+        // levels lb..L in one CTA
+        BottomArgs ba = m->bottom;
+        ba.b_in = b;
+        ba.z_out = L.z;
+        k_cycle_bottom<<<1, kBottomThreads, m->bottom_smem, s>>>(ba, ss);
         c->launches++;
         return;
     }
