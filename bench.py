@@ -301,7 +301,7 @@ def _peaks():
         return {}
 
 
-TRAIN_AT = (4, 8, 12, 16, 20)     # OC iterations after which snapshots are taken
+TRAIN_AT = (8, 16, 24, 32, 40)    # OC iterations after which snapshots are taken
 TRAIN_SNAPS = 2                    # snapshots per design
 TRAIN_STEPS = 20
 
