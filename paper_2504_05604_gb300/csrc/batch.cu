@@ -327,53 +327,6 @@ static cudaError_t build_iter_graph(to3d_ctx* c) {
     return e;
 }
 
-// ------------------------------------------------------------------ autotuner
-// The tensor-core kernel walks z segments of lz node layers per tile.  Short
-// segments give more tiles (better balance on small grids), long ones less
-// halo.  The best lz is timed once per grid shape and precision and cached.
-static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int, int>, int> g_tune;
-
-static cudaError_t autotune_tc(to3d_ctx* c) {
-    const auto key = std::make_tuple(c->g.nx, c->g.ny, c->g.nz, c->prm.precision);
-    {
-        std::lock_guard<std::mutex> lock(g_tune_mu);
-        auto it = g_tune.find(key);
-        if (it != g_tune.end()) {
-            c->tc_lz = it->second;
-            return cudaSuccess;
-        }
-    }
-    launch_simp(c, c->stream, c->x);
-    const int cand[] = {4, 6, 8, 12, 16, 20, 27, 40, 81};
-    cudaEvent_t e0, e1;
-    CE(cudaEventCreate(&e0));
-    CE(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int best_lz = c->tc_lz;
-    for (int lz : cand) {
-        if (lz > c->g.nz && lz != cand[0]) continue;
-        c->tc_lz = lz;
-        launch_matvec_tc(c, c->stream, c->prm.precision, false, 0);
-        CE(cudaEventRecord(e0, c->stream));
-        for (int r = 0; r < 3; ++r) launch_matvec_tc(c, c->stream, c->prm.precision, false, 0);
-        CE(cudaEventRecord(e1, c->stream));
-        CE(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CE(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-            best = ms;
-            best_lz = lz;
-        }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    c->tc_lz = best_lz;
-    std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune[key] = best_lz;
-    return cudaGetLastError();
-}
-
 }  // namespace to3d
 
 using namespace to3d;
@@ -448,7 +401,7 @@ to3d_status to3d_batch_create(int32_t nprob, const to3d_params* params, const ui
             cudaMemcpy(c->dcctl, &h, sizeof(DcCtl), cudaMemcpyHostToDevice) != cudaSuccess ||
             (c->prm.filter == TO3D_FILTER_DENS &&
              cudaMalloc(&c->xphys, sizeof(double) * c->g.nel) != cudaSuccess) ||
-            autotune_tc(c) != cudaSuccess ||
+            tune_tc_lz(c, c->prm.precision, c->tm_pa, c->q32, true) != cudaSuccess ||
             (c->prm.precond == TO3D_LMG && mg_capture_ready(c) != TO3D_OK) ||
             build_iter_graph(c) != cudaSuccess) {
             batch_free(b);

@@ -202,6 +202,10 @@ void launch_matvec_tc_io(to3d_ctx* c, cudaStream_t s, int prec, bool fused, cons
                          const CUtensorMap& tp, const CUtensorMap& td, float* p_new, float* q,
                          SolverScalars* ss);
 bool encode_vec_map(to3d_ctx* c, CUtensorMap* map, const float* base, int comps);
+// time the tensor-core kernel's z-segment lengths once per grid shape and
+// precision (cached) and keep the fastest in c->tc_lz (plain form, input
+// mapped by tp, output q)
+cudaError_t tune_tc_lz(to3d_ctx* c, int prec, const CUtensorMap& tp, float* q, bool set_moduli);
 void launch_aos_to_soa(to3d_ctx* c, cudaStream_t s, const float* in, float* out);
 void launch_soa_to_aos(to3d_ctx* c, cudaStream_t s, const float* q, const float* p, float* y);
 void init_tc_attributes();

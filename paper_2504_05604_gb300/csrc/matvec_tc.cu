@@ -50,6 +50,9 @@
 //   3  FP16:    p_e scaled by a power of two so max|p_e| lies in [2^10, 2^11)
 //   4  FP16X2:  the scaled p_e as FP16 hi + lo slices (about 22 significant bits)
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include <cuda.h>
@@ -902,6 +905,59 @@ __global__ void k_selftest_wait(int polls, int* status) {
     tc::fence_mbar_init();
     const bool ok = tc::mbar_wait_sleep_bounded(&bar, 0u, (uint32_t)polls, 1000u);
     *status = ok ? (int)TO3D_OK : (int)TO3D_ETIMEOUT;
+}
+
+// ------------------------------------------------------------------ autotuner
+// The tensor-core kernel walks z segments of lz node layers per tile.  Short
+// segments give more tiles (better balance on small grids), long ones less
+// halo.  The best lz is timed once per grid shape and precision and cached.
+// The timing runs the plain form with precision prec on the input mapped by
+// tp and writes q; set_moduli first fills E32 from x, otherwise whatever E32
+// holds is used (the time does not depend on the values).
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int>, int> g_tune;
+
+cudaError_t tune_tc_lz(to3d_ctx* c, int prec, const CUtensorMap& tp, float* q, bool set_moduli) {
+    const auto key = std::make_tuple(c->g.nx, c->g.ny, c->g.nz, prec);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            c->tc_lz = it->second;
+            return cudaSuccess;
+        }
+    }
+    if (set_moduli) launch_simp(c, c->stream, c->x);
+    const int cand[] = {4, 6, 8, 12, 16, 20, 27, 40, 81};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_lz = c->tc_lz;
+    for (int lz : cand) {
+        if (err != cudaSuccess) break;
+        if (lz > c->g.nz && lz != cand[0]) continue;
+        c->tc_lz = lz;
+        auto op = [&]() { launch_matvec_tc_io(c, c->stream, prec, false, c->tm_r, tp, c->tm_d, nullptr, q, nullptr); };
+        op();
+        err = cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < 3 && err == cudaSuccess; ++r) op();
+        if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err == cudaSuccess && ms < best) {
+            best = ms;
+            best_lz = lz;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    c->tc_lz = best_lz;
+    if (err != cudaSuccess) return err;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = best_lz;
+    return cudaGetLastError();
 }
 
 }  // namespace to3d

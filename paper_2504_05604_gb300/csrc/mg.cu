@@ -35,6 +35,7 @@
 // rounding, so it serves flexible CG in FP64 (TO3D_F64) and an FP32 inner
 // CG inside the FP64 defect correction (the *_DC forms).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -188,8 +189,10 @@ __global__ void k_jacobi(long long vol, const float* __restrict__ b, const float
     }
 }
 
-// b_c = R (b_f - t_f): each coarse node gathers the 27 fine nodes 2C + d,
-// weights prod (1 - |d| / 2); clamped dofs of either grid contribute 0
+// Restriction: b_c = R (b_f - t_f), each coarse node gathering the 27 fine
+// nodes 2C + d with weights prod (1 - |d| / 2); clamped dofs of either grid
+// contribute 0.  The 27 points are unrolled (bounds as predicates), so all
+// their loads are in flight together.
 __global__ void k_restrict(const Grid gf, int pxf, long long volf, const float* __restrict__ bf,
                            const float* __restrict__ tf, const uint8_t* __restrict__ maskf,
                            const Grid gc, int pxc, long long volc, const uint8_t* __restrict__ maskc,
@@ -197,20 +200,20 @@ __global__ void k_restrict(const Grid gf, int pxf, long long volf, const float* 
     if (skip(ss)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     if (i >= gc.nx) return;
+    const long long planef = (long long)pxf * gf.ny;
+    const long long base = 2 * i + (long long)pxf * (2 * j) + planef * (2 * k);
     float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
     for (int dk = -1; dk <= 1; ++dk) {
-        const int fk = 2 * k + dk;
-        if (fk < 0 || fk >= gf.nz) continue;
-        const float wk = dk ? 0.5f : 1.f;
+        const bool okk = 2 * k + dk >= 0 && 2 * k + dk < gf.nz;
+#pragma unroll
         for (int dj = -1; dj <= 1; ++dj) {
-            const int fj = 2 * j + dj;
-            if (fj < 0 || fj >= gf.ny) continue;
-            const float wj = wk * (dj ? 0.5f : 1.f);
+            const bool okj = okk && 2 * j + dj >= 0 && 2 * j + dj < gf.ny;
+#pragma unroll
             for (int di = -1; di <= 1; ++di) {
-                const int fi = 2 * i + di;
-                if (fi < 0 || fi >= gf.nx) continue;
-                const float wt = wj * (di ? 0.5f : 1.f);
-                const long long p = fi + (long long)pxf * (fj + (long long)gf.ny * fk);
+                if (!(okj && 2 * i + di >= 0 && 2 * i + di < gf.nx)) continue;
+                const float wt = (di ? 0.5f : 1.f) * (dj ? 0.5f : 1.f) * (dk ? 0.5f : 1.f);
+                const long long p = base + di + (long long)pxf * dj + planef * dk;
                 const uint8_t m = maskf[p];
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
@@ -224,22 +227,31 @@ __global__ void k_restrict(const Grid gf, int pxf, long long volf, const float* 
     for (int c = 0; c < 3; ++c) bc[c * volc + pc] = ((mc >> c) & 1) ? 0.f : acc[c];
 }
 
-// z_f += P z_c (trilinear), clamped fine dofs untouched (they stay 0)
+// Prolongation z_f += P z_c (trilinear), clamped fine dofs untouched (they
+// stay 0), in two forms with the same arithmetic.
+//
+// k_prolong: one thread per fine node (2C + d gathers the coarse nodes C..C+1
+// along the odd axes, weight 1/2 per odd axis); the eight candidates are
+// unrolled with predicates.  Used on the small grids, where latency rules.
 __global__ void k_prolong(const Grid gf, int pxf, long long volf, const uint8_t* __restrict__ maskf,
                           float* __restrict__ zf, const Grid gc, int pxc, long long volc,
                           const float* __restrict__ zc, const SolverScalars* ss) {
     if (skip(ss)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     if (i >= gf.nx) return;
-    const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
-    const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
-    const float wi = (i & 1) ? 0.5f : 1.f, wj = (j & 1) ? 0.5f : 1.f, wk = (k & 1) ? 0.5f : 1.f;
+    const bool ox = i & 1, oy = j & 1, oz = k & 1;
+    const float w = (ox ? 0.5f : 1.f) * (oy ? 0.5f : 1.f) * (oz ? 0.5f : 1.f);
+    const long long planec = (long long)pxc * gc.ny;
+    const long long base = (i >> 1) + (long long)pxc * (j >> 1) + planec * (k >> 1);
     float acc[3] = {0.f, 0.f, 0.f};
-    for (int a = 0; a < nk; ++a)
-        for (int bb = 0; bb < nj; ++bb)
-            for (int cc = 0; cc < ni; ++cc) {
-                const long long p = (i0 + cc) + (long long)pxc * ((j0 + bb) + (long long)gc.ny * (k0 + a));
-                const float w = wi * wj * wk;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                if ((cc && !ox) || (bb && !oy) || (a && !oz)) continue;
+                const long long p = base + cc + (long long)pxc * bb + planec * a;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) acc[c] = fmaf(w, zc[c * volc + p], acc[c]);
             }
@@ -248,6 +260,74 @@ __global__ void k_prolong(const Grid gf, int pxf, long long volf, const uint8_t*
 #pragma unroll
     for (int c = 0; c < 3; ++c)
         if (!((m >> c) & 1)) zf[c * volf + pf] += acc[c];
+}
+
+// k_prolong_col: one thread per coarse node (i, j, k), 32 consecutive i per
+// warp, adding to the fine nodes (2i + a, 2j + b, 2k + c), a, b, c in {0, 1},
+// from the coarse nodes (i..i+1, j..j+1, k..k+1) with the trilinear weights
+// applied axis by axis; the i + 1 neighbour comes from the next lane by
+// warp shuffle.  Each coarse value is loaded once per thread instead of
+// once per fine node: used on the large grids, where instructions rule.
+constexpr int kColX = 32, kColY = 4;
+__global__ void __launch_bounds__(kColX * kColY)
+    k_prolong_col(const Grid gf, int pxf, long long volf, const uint8_t* __restrict__ maskf,
+                  float* __restrict__ zf, const Grid gc, int pxc, long long volc,
+                  const float* __restrict__ zc, const SolverScalars* ss) {
+    if (skip(ss)) return;
+    const int lane = threadIdx.x;
+    const int i = blockIdx.x * kColX + lane, j = blockIdx.y * kColY + threadIdx.y, k = blockIdx.z;
+    // no early return below: the shuffles need every lane of the warp
+    const bool col = i < gc.nx && j < gc.ny;
+    const long long planec = (long long)pxc * gc.ny, planef = (long long)pxf * gf.ny;
+    const bool okj1 = j + 1 < gc.ny;
+    // X[b][a][c]: the x-interpolated coarse values of row j + b at fine x
+    // offset a, for one coarse layer
+    auto load = [&](int kl, float (&X)[2][2][3]) {
+        const bool kok = col && kl < gc.nz;
+        const long long p = kok ? i + (long long)pxc * j + planec * kl : 0;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const bool ok = kok && (b == 0 || okj1);
+            const long long pb = p + (b ? pxc : 0);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float z0 = ok ? zc[c * volc + pb] : 0.f;
+                float z1 = __shfl_down_sync(0xffffffffu, z0, 1);
+                if (lane == kColX - 1) z1 = (ok && i + 1 < gc.nx) ? zc[c * volc + pb + 1] : 0.f;
+                X[b][0][c] = z0;
+                X[b][1][c] = 0.5f * (z0 + z1);
+            }
+        }
+    };
+    float Xk[2][2][3], Xn[2][2][3];
+    load(k, Xk);
+    load(k + 1, Xn);
+    if (!col) return;
+#pragma unroll
+    for (int cz = 0; cz < 2; ++cz) {
+        const int fk = 2 * k + cz;
+        if (fk >= gf.nz) continue;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int fj = 2 * j + b;
+            if (fj >= gf.ny) continue;
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const int fi = 2 * i + a;
+                if (fi >= gf.nx) continue;
+                const long long pf = fi + (long long)pxf * fj + planef * fk;
+                const uint8_t m = maskf[pf];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    // y then z interpolation of the x-interpolated values
+                    const float lo = b ? 0.5f * (Xk[0][a][c] + Xk[1][a][c]) : Xk[0][a][c];
+                    const float hi = b ? 0.5f * (Xn[0][a][c] + Xn[1][a][c]) : Xn[0][a][c];
+                    const float v = cz ? 0.5f * (lo + hi) : lo;
+                    if (!((m >> c) & 1)) zf[c * volf + pf] += v;
+                }
+            }
+        }
+    }
 }
 
 // coarse moduli: s (sum over the 8 child slots of E^q / 8)^(1/q), missing 0
@@ -316,6 +396,24 @@ __global__ void k_fill(long long n, float v, float* __restrict__ a) {
         a[i] = v;
 }
 
+// beta of the inner MG-PCG from rz = r.z and zq = z.q_old (see below)
+__device__ __forceinline__ void set_beta(SolverScalars* ss, double rzn, double zq) {
+    const bool first = ss->pad0 != 0;
+    // right after a residual replacement the recurrence r_new - r_old =
+    // -alpha q_old no longer holds: Fletcher-Reeves beta once
+    const bool fr = ss->pad1 != 0;
+    const double beta = first ? 0.0 : (fr ? rzn / ss->rz : -ss->alpha * zq / ss->rz);
+    ss->pad0 = 0;
+    ss->pad1 = 0;
+    ss->beta = beta;
+    ss->zcoef = 1.0;
+    ss->rz = rzn;
+    if (!(rzn > 0.0) || !isfinite(rzn) || !isfinite(beta)) {
+        ss->status = TO3D_ENUMERIC;
+        ss->done = 1;
+    }
+}
+
 // Inner MG-PCG, after the cycle z = V r: rz = r.z and z.q_old give the
 // Polak-Ribiere coefficient beta = z_new.(r_new - r_old) / rz_old
 // = -alpha z_new.q_old / rz_old (0 on the first step of a segment).
@@ -338,23 +436,61 @@ __global__ void k_pcg_dots(long long vol, const float* __restrict__ r, const flo
         zq += (double)fmaf(b.x, c4.x, fmaf(b.y, c4.y, fmaf(b.z, c4.z, b.w * c4.w)));
     }
     double v[2] = {rz, zq};
-    if (grid_sum<2>(red, v, sh, out) && threadIdx.x == 0) {
-        const double rzn = out[0];
-        const bool first = ss->pad0 != 0;
-        // right after a residual replacement the recurrence r_new - r_old =
-        // -alpha q_old no longer holds: Fletcher-Reeves beta once
-        const bool fr = ss->pad1 != 0;
-        const double beta = first ? 0.0 : (fr ? rzn / ss->rz : -ss->alpha * out[1] / ss->rz);
-        ss->pad0 = 0;
-        ss->pad1 = 0;
-        ss->beta = beta;
-        ss->zcoef = 1.0;
-        ss->rz = rzn;
-        if (!(rzn > 0.0) || !isfinite(rzn) || !isfinite(beta)) {
-            ss->status = TO3D_ENUMERIC;
-            ss->done = 1;
+    if (grid_sum<2>(red, v, sh, out) && threadIdx.x == 0) set_beta(ss, out[0], out[1]);
+}
+
+// The level-0 cycle's last smoothing sweep, z += w D^-1 (b - t) with b = r,
+// fused with the two dots of k_pcg_dots (r.z and z.q_old) and its beta.
+// Four consecutive nodes per step (vol is a multiple of 4: 16-byte loads,
+// 14 of them in flight per thread); FP32 partial sums of the 12 products of
+// a step, FP64 across steps, blocks and the grid (one FP64 add per node
+// would load this GPU's narrow FP64 pipe).
+__global__ void __launch_bounds__(256)
+    k_jacobi_dots(long long vol, const float* __restrict__ b, const float* __restrict__ t,
+                  const float* __restrict__ dinv, const uint8_t* __restrict__ maskp,
+                  const float* __restrict__ wdev, float* __restrict__ z, const float* __restrict__ q,
+                  const Reducer red, SolverScalars* ss) {
+    if (ss->done) return;
+    __shared__ double sh[64];
+    __shared__ double out[2];
+    const float w = wdev[0];
+    const long long v4 = vol >> 2;
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+    const float4* t4 = reinterpret_cast<const float4*>(t);
+    const float4* q4 = reinterpret_cast<const float4*>(q);
+    const float4* di4 = reinterpret_cast<const float4*>(dinv);
+    const uchar4* m4 = reinterpret_cast<const uchar4*>(maskp);
+    float4* z4 = reinterpret_cast<float4*>(z);
+    double rz = 0.0, zq = 0.0;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < v4;
+         n += (long long)gridDim.x * blockDim.x) {
+        const float4 di = __ldg(di4 + n);
+        const uchar4 mk = __ldg(m4 + n);
+        float4 bb[3], tt[3], zz[3], qq[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            bb[c] = __ldg(b4 + c * v4 + n);
+            tt[c] = __ldg(t4 + c * v4 + n);
+            zz[c] = z4[c * v4 + n];
+            qq[c] = __ldg(q4 + c * v4 + n);
         }
+        float prz = 0.f, pzq = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float4 zv;
+            zv.x = ((mk.x >> c) & 1) ? 0.f : fmaf(w * di.x, bb[c].x - tt[c].x, zz[c].x);
+            zv.y = ((mk.y >> c) & 1) ? 0.f : fmaf(w * di.y, bb[c].y - tt[c].y, zz[c].y);
+            zv.z = ((mk.z >> c) & 1) ? 0.f : fmaf(w * di.z, bb[c].z - tt[c].z, zz[c].z);
+            zv.w = ((mk.w >> c) & 1) ? 0.f : fmaf(w * di.w, bb[c].w - tt[c].w, zz[c].w);
+            z4[c * v4 + n] = zv;
+            prz = fmaf(bb[c].x, zv.x, fmaf(bb[c].y, zv.y, fmaf(bb[c].z, zv.z, fmaf(bb[c].w, zv.w, prz))));
+            pzq = fmaf(zv.x, qq[c].x, fmaf(zv.y, qq[c].y, fmaf(zv.z, qq[c].z, fmaf(zv.w, qq[c].w, pzq))));
+        }
+        rz += (double)prz;
+        zq += (double)pzq;
     }
+    double v[2] = {rz, zq};
+    if (grid_sum<2>(red, v, sh, out) && threadIdx.x == 0) set_beta(ss, out[0], out[1]);
 }
 
 // Segment start: r32 = scale r64 (masked), d = 0, p_old = 0, q = 0; |r32|^2
@@ -420,16 +556,17 @@ __global__ void k_pow_dots(long long vol, const float* __restrict__ z, const flo
                            const Reducer red, double* out_dev) {
     __shared__ double sh[64];
     __shared__ double o2[2];
-    // FP32 products and per-node partial sums (a Rayleigh quotient needs no
-    // more), FP64 across nodes, blocks and the grid
+    // FP32 products and partial sums over up to 8 nodes (a Rayleigh quotient
+    // needs no more), FP64 beyond, across blocks and the grid
     double a = 0.0, b = 0.0;
+    float pa = 0.f, pb = 0.f;
+    int cnt = 0;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < vol;
          n += (long long)gridDim.x * blockDim.x) {
         const float di = dinv[n];
         const uint8_t m = maskp[n];
         if (!(di > 0.f)) continue;
         const float dn = 1.f / di;
-        float pa = 0.f, pb = 0.f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             if ((m >> c) & 1) continue;
@@ -437,9 +574,15 @@ __global__ void k_pow_dots(long long vol, const float* __restrict__ z, const flo
             pa = fmaf(zv, t[c * vol + n], pa);
             pb = fmaf(zv * zv, dn, pb);
         }
-        a += (double)pa;
-        b += (double)pb;
+        if (++cnt == 8) {
+            a += (double)pa;
+            b += (double)pb;
+            pa = pb = 0.f;
+            cnt = 0;
+        }
     }
+    a += (double)pa;
+    b += (double)pb;
     double v[2] = {a, b};
     if (grid_sum<2>(red, v, sh, o2) && threadIdx.x == 0) {
         out_dev[0] = o2[0];
@@ -472,11 +615,56 @@ __global__ void k_pow_final(const double* __restrict__ out, double w, double mar
     lam_out[l] = lam_ok;
 }
 
+// t += K z over the elements of one bottom level, TPE threads per element:
+// each thread gathers its element's 24 values of z and forms the rows of
+// 8 / TPE local nodes (row by row from float4 reads of the unit KE in shared
+// memory), scaled by E_e and added into t with shared-memory atomics.  More
+// threads per element shorten the dependent chains on the small levels.
+template <int TPE>
+__device__ __forceinline__ void bottom_op_items(const Grid& g, const float* __restrict__ Ks,
+                                                const float* z, float* t, const float* Es, int tid,
+                                                int nt) {
+    constexpr int NQ = 8 / TPE;
+    const int nel = (int)g.nel, nelx = g.nelx, nely = g.nely, nx = g.nx, ny = g.ny;
+    for (int w = tid; w < TPE * nel; w += nt) {
+        const int e = w / TPE, part = w - e * TPE;
+        const int ei = e % nelx, ej = (e / nelx) % nely, ek = e / (nelx * nely);
+        const int n0 = ei + nx * (ej + ny * ek);
+        float ze[24];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int nd = n0 + (q & 1) + nx * (((q >> 1) & 1) + ny * (q >> 2));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ze[3 * q + c] = z[3 * nd + c];
+        }
+        const float Ee = Es[e];
+#pragma unroll
+        for (int qq = 0; qq < NQ; ++qq) {
+            const int q = part * NQ + qq;
+            const int nd = n0 + (q & 1) + nx * (((q >> 1) & 1) + ny * (q >> 2));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float4* row = reinterpret_cast<const float4*>(Ks + (3 * q + c) * 24);
+                float acc = 0.f;
+#pragma unroll
+                for (int k4 = 0; k4 < 6; ++k4) {
+                    const float4 kv = row[k4];
+                    acc = fmaf(kv.x, ze[4 * k4 + 0], acc);
+                    acc = fmaf(kv.y, ze[4 * k4 + 1], acc);
+                    acc = fmaf(kv.z, ze[4 * k4 + 2], acc);
+                    acc = fmaf(kv.w, ze[4 * k4 + 3], acc);
+                }
+                atomicAdd(&t[3 * nd + c], Ee * acc);
+            }
+        }
+    }
+}
+
 // The V-cycle over the bottom levels in one CTA.  Levels lb..L whose
 // vectors, damping, clamp bits and moduli fit in shared memory together
 // (kBottomSmem) run inside one kernel: every operator application element by
 // element in FP32 on the CUDA cores (24 x 24 products, shared-memory atomics
-// into the nodes), restriction, prolongation and the damped-Jacobi sweeps
+// into the nodes; bottom_op_items), restriction, prolongation and the damped-Jacobi sweeps
 // as in the per-level kernels, __syncthreads between the steps.  On the
 // largest grids that is the last four levels, whose per-level launches were
 // bound by launch latency.
@@ -500,9 +688,8 @@ __global__ void __launch_bounds__(kBottomThreads, 1)
             if (li == 0)
                 for (int c = 0; c < 3; ++c) bsm[L.ob + 3 * n + c] = a.b_in[c * L.vol + p];
         }
-        for (long long e = tid; e < L.g.nel; e += nt) {
-            const int ei = (int)(e % L.g.nelx), ej = (int)((e / L.g.nelx) % L.g.nely),
-                      ek = (int)(e / ((long long)L.g.nelx * L.g.nely));
+        for (int e = tid; e < (int)L.g.nel; e += nt) {
+            const int ei = e % L.g.nelx, ej = (e / L.g.nelx) % L.g.nely, ek = e / (L.g.nelx * L.g.nely);
             bsm[L.oE + e] = L.E32[ei + (long long)L.pex * (ej + (long long)L.g.nely * ek)];
         }
     }
@@ -511,31 +698,15 @@ __global__ void __launch_bounds__(kBottomThreads, 1)
     // t = K z on level li
     auto op = [&](int li) {
         const BottomLevel& L = a.L[li];
-        const int nn = (int)L.g.nnode;
-        float* z = bsm + L.oz;
+        const int nn = (int)L.g.nnode, nel = (int)L.g.nel;
+        const float* z = bsm + L.oz;
         float* t = bsm + L.ot;
         for (int i = tid; i < 3 * nn; i += nt) t[i] = 0.f;
         __syncthreads();
-        for (long long e = tid; e < L.g.nel; e += nt) {
-            const int ei = (int)(e % L.g.nelx), ej = (int)((e / L.g.nelx) % L.g.nely),
-                      ek = (int)(e / ((long long)L.g.nelx * L.g.nely));
-            int nd[8];
-            float ze[24];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                nd[q] = (ei + (q & 1)) + L.g.nx * ((ej + ((q >> 1) & 1)) + L.g.ny * (ek + (q >> 2)));
-#pragma unroll
-                for (int c = 0; c < 3; ++c) ze[3 * q + c] = z[3 * nd[q] + c];
-            }
-            const float Ee = bsm[L.oE + e];
-#pragma unroll 4
-            for (int r = 0; r < 24; ++r) {
-                float acc = 0.f;
-#pragma unroll
-                for (int k = 0; k < 24; ++k) acc = fmaf(Ks[r * 24 + k], ze[k], acc);
-                atomicAdd(&t[3 * nd[r / 3] + r % 3], Ee * acc);
-            }
-        }
+        if (8 * nel <= nt) bottom_op_items<8>(L.g, Ks, z, t, bsm + L.oE, tid, nt);
+        else if (4 * nel <= nt) bottom_op_items<4>(L.g, Ks, z, t, bsm + L.oE, tid, nt);
+        else if (2 * nel <= nt) bottom_op_items<2>(L.g, Ks, z, t, bsm + L.oE, tid, nt);
+        else bottom_op_items<1>(L.g, Ks, z, t, bsm + L.oE, tid, nt);
         __syncthreads();
     };
     // z = d b (first sweep from 0) or z += d (b - t)
@@ -553,7 +724,7 @@ __global__ void __launch_bounds__(kBottomThreads, 1)
         }
         __syncthreads();
     };
-    // b_{li+1} = R (b_li - t_li)
+    // b_{li+1} = R (b_li - t_li); the 27 points unrolled (bounds as predicates)
     auto restrict_to = [&](int li) {
         const BottomLevel& F = a.L[li];
         const BottomLevel& C = a.L[li + 1];
@@ -561,22 +732,26 @@ __global__ void __launch_bounds__(kBottomThreads, 1)
         for (int n = tid; n < nc; n += nt) {
             const int i = n % C.g.nx, j = (n / C.g.nx) % C.g.ny, k = n / (C.g.nx * C.g.ny);
             float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
             for (int dk = -1; dk <= 1; ++dk) {
                 const int fk = 2 * k + dk;
-                if (fk < 0 || fk >= F.g.nz) continue;
+                const bool okk = fk >= 0 && fk < F.g.nz;
+#pragma unroll
                 for (int dj = -1; dj <= 1; ++dj) {
                     const int fj = 2 * j + dj;
-                    if (fj < 0 || fj >= F.g.ny) continue;
+                    const bool okj = okk && fj >= 0 && fj < F.g.ny;
+#pragma unroll
                     for (int di = -1; di <= 1; ++di) {
                         const int fi = 2 * i + di;
-                        if (fi < 0 || fi >= F.g.nx) continue;
+                        if (!(okj && fi >= 0 && fi < F.g.nx)) continue;
                         const float wt = (dk ? 0.5f : 1.f) * (dj ? 0.5f : 1.f) * (di ? 0.5f : 1.f);
                         const int f = fi + F.g.nx * (fj + F.g.ny * fk);
                         const uint8_t m = bytes[F.om + f];
 #pragma unroll
-                        for (int c = 0; c < 3; ++c)
-                            if (!((m >> c) & 1))
-                                acc[c] = fmaf(wt, bsm[F.ob + 3 * f + c] - bsm[F.ot + 3 * f + c], acc[c]);
+                        for (int c = 0; c < 3; ++c) {
+                            const float v = bsm[F.ob + 3 * f + c] - bsm[F.ot + 3 * f + c];
+                            acc[c] = fmaf(((m >> c) & 1) ? 0.f : wt, v, acc[c]);
+                        }
                     }
                 }
             }
@@ -586,21 +761,25 @@ __global__ void __launch_bounds__(kBottomThreads, 1)
         }
         __syncthreads();
     };
-    // z_li += P z_{li+1}
+    // z_li += P z_{li+1}; the eight candidates unrolled (predicates)
     auto prolong_from = [&](int li) {
         const BottomLevel& F = a.L[li];
         const BottomLevel& C = a.L[li + 1];
         const int nf = (int)F.g.nnode;
         for (int n = tid; n < nf; n += nt) {
             const int i = n % F.g.nx, j = (n / F.g.nx) % F.g.ny, k = n / (F.g.nx * F.g.ny);
-            const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
-            const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
-            const float w = ((i & 1) ? 0.5f : 1.f) * ((j & 1) ? 0.5f : 1.f) * ((k & 1) ? 0.5f : 1.f);
+            const bool ox = i & 1, oy = j & 1, oz = k & 1;
+            const float w = (ox ? 0.5f : 1.f) * (oy ? 0.5f : 1.f) * (oz ? 0.5f : 1.f);
+            const int c0 = (i >> 1) + C.g.nx * ((j >> 1) + C.g.ny * (k >> 1));
             float acc[3] = {0.f, 0.f, 0.f};
-            for (int aa = 0; aa < nk; ++aa)
-                for (int bb = 0; bb < nj; ++bb)
-                    for (int cc = 0; cc < ni; ++cc) {
-                        const int cn = (i0 + cc) + C.g.nx * ((j0 + bb) + C.g.ny * (k0 + aa));
+#pragma unroll
+            for (int aa = 0; aa < 2; ++aa)
+#pragma unroll
+                for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+                    for (int cc = 0; cc < 2; ++cc) {
+                        if ((cc && !ox) || (bb && !oy) || (aa && !oz)) continue;
+                        const int cn = c0 + cc + C.g.nx * (bb + C.g.ny * aa);
 #pragma unroll
                         for (int c = 0; c < 3; ++c) acc[c] = fmaf(w, bsm[C.oz + 3 * cn + c], acc[c]);
                     }
@@ -823,6 +1002,10 @@ static to3d_status ensure_mg(to3d_ctx* c) {
                                        kBottomSmem));
         }
     }
+    // z-segment length of the tensor-core kernel per launched level (the
+    // coarse grids are small: shorter segments give more CTAs)
+    for (int l = 0; l < m->lb && l < (int)m->lv.size(); ++l)
+        MG_CK(tune_tc_lz(m->lv[l].ctx, m->prec, m->lv[l].tm_z, m->lv[l].t, false));
     const long long ndof = 3 * g0.nnode;
     MG_CK(cudaMalloc(&m->wdev, sizeof(float) * kMaxLevels));
     MG_CK(cudaMalloc(&m->lamdev, sizeof(double) * kMaxLevels));
@@ -894,8 +1077,10 @@ static to3d_status setup_levels(to3d_ctx* c) {
 }
 
 // One V-cycle from level l: b (padded SoA of level l) -> lv[l].z.
+// fuse_dots (level 0 of the inner MG-PCG only): the last sweep also forms
+// r.z, z.q_old and beta (k_jacobi_dots), so no separate k_pcg_dots.
 static void cycle_launch(to3d_ctx* c, Mg* m, cudaStream_t s, size_t l, const float* b,
-                         SolverScalars* ss) {
+                         SolverScalars* ss, bool fuse_dots = false) {
     Level& L = m->lv[l];
     to3d_ctx* k = L.ctx;
     const long long vol = k->vol;
@@ -937,10 +1122,24 @@ static void cycle_launch(to3d_ctx* c, Mg* m, cudaStream_t s, size_t l, const flo
         k->g, k->px, vol, b, L.t, k->maskp, kc->g, kc->px, kc->vol, kc->maskp, kc->r32, ss);
     c->launches++;
     cycle_launch(c, m, s, l + 1, kc->r32, ss);
-    k_prolong<<<dim3((k->g.nx + 127) / 128, k->g.ny, k->g.nz), 128, 0, s>>>(
-        k->g, k->px, vol, k->maskp, L.z, kc->g, kc->px, kc->vol, C.z, ss);
+    if (k->g.nnode >= (1LL << 22))
+        k_prolong_col<<<dim3((kc->g.nx + kColX - 1) / kColX, (kc->g.ny + kColY - 1) / kColY, kc->g.nz),
+                        dim3(kColX, kColY), 0, s>>>(k->g, k->px, vol, k->maskp, L.z, kc->g, kc->px,
+                                                    kc->vol, C.z, ss);
+    else
+        k_prolong<<<dim3((k->g.nx + 127) / 128, k->g.ny, k->g.nz), 128, 0, s>>>(
+            k->g, k->px, vol, k->maskp, L.z, kc->g, kc->px, kc->vol, C.z, ss);
     c->launches++;
-    for (int i = 0; i < m->nu; ++i) sweep();     // post-smoothing
+    for (int i = 0; i < m->nu; ++i) {             // post-smoothing
+        if (fuse_dots && i + 1 == m->nu) {
+            op();
+            k_jacobi_dots<<<nblocks(vol / 4), 256, 0, s>>>(vol, b, L.t, k->dinv32, k->maskp, m->wdev,
+                                                          L.z, c->q32, c->red, ss);
+            c->launches++;
+        } else {
+            sweep();
+        }
+    }
 }
 
 // Make sure the hierarchy belongs to the current fine operator.
@@ -997,10 +1196,15 @@ namespace to3d {
 // ev0/ev1 (may be null): external events recorded around the fused kernel.
 static void mgpcg_iter(to3d_ctx* c, Mg* m, cudaStream_t s, int prec, int parity,
                        cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
-    cycle_launch(c, m, s, 0, c->r32, c->ss);
-    k_pcg_dots<<<nblocks(3 * c->vol), kThreads, 0, s>>>(c->vol, c->r32, m->lv[0].z, c->q32, c->red,
-                                                        c->ss);
-    c->launches++;
+    // with level 0 above the one-CTA bottom cycle the dots ride on its last
+    // sweep; otherwise a separate pass
+    const bool fused = m->lb > 0;
+    cycle_launch(c, m, s, 0, c->r32, c->ss, fused);
+    if (!fused) {
+        k_pcg_dots<<<nblocks(3 * c->vol), kThreads, 0, s>>>(c->vol, c->r32, m->lv[0].z, c->q32,
+                                                            c->red, c->ss);
+        c->launches++;
+    }
     float* p_new = parity ? c->p32b : c->p32a;
     const CUtensorMap& tp = parity ? c->tm_pa : c->tm_pb;
     if (ev0) cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal);
@@ -1091,8 +1295,10 @@ to3d_status solve_dc_mg(to3d_ctx* c, const double* f, double fnorm, to3d_solve_i
                 delta * delta, t * t);
         }
         c->launches++;
-        int it0 = 0;
+        int it0 = 0, chunks = 0;
+        const auto seg_t0 = std::chrono::steady_clock::now();
         for (;;) {
+            ++chunks;
             if ((st = mgpcg_chunk(c, m, prec, kMgChunk))) return st;
             if ((st = sync_solver_scalars(c))) return st;
             accumulate_tc_times(c, it0, c->ss_h->it);
@@ -1113,9 +1319,14 @@ to3d_status solve_dc_mg(to3d_ctx* c, const double* f, double fnorm, to3d_solve_i
         // recurrence ran away from it): then restart from it
         restart = !keep || relres > 0.5 * prev;
         if (restart) scale = 0.0;
-        if (c->trace)
-            std::fprintf(stderr, "to3d: mg segment %d: %d inner its (total %d), relres %.3e -> %.3e\n",
-                         outer, its, total, prev, relres);
+        if (c->trace) {
+            const double seg_ms =
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - seg_t0).count();
+            std::fprintf(stderr,
+                         "to3d: mg segment %d: %d inner its in %d chunks (total %d), relres %.3e -> %.3e, "
+                         "%.2f ms wall (host, incl. the FP64 residual)\n",
+                         outer, its, chunks, total, prev, relres, seg_ms);
+        }
         if (relres <= tol) break;
         ++outer;
         if (total >= c->prm.cg_maxit || outer >= 1000) {

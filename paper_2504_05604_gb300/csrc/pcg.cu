@@ -179,12 +179,15 @@ __global__ void k_pcg32_init(const Grid g, int px, long long vol, const double* 
 
 // d += alpha p, r -= alpha q (clamped dofs and pads kept at 0), rz_new, rr,
 // beta, flags.  Four consecutive nodes per step (vol is a multiple of 4), so
-// every thread keeps 14 independent 16-byte loads in flight.
+// every thread keeps 14 independent 16-byte loads in flight.  Without the
+// Jacobi beta (JB = 0: the caller forms beta) M^-1 is neither read nor used.
+template <int JB>
 __global__ void __launch_bounds__(256)
     k_pcg32_update(long long vol, float* __restrict__ d32, float* __restrict__ r32,
                    const float* __restrict__ p, const float* __restrict__ q,
                    const float* __restrict__ dinv, const uint8_t* __restrict__ maskp,
-                   const Reducer red, SolverScalars* ss, int jacobi_beta) {
+                   const Reducer red, SolverScalars* ss) {
+    constexpr int jacobi_beta = JB;
     if (ss->done) return;
     __shared__ double sh[64];
     __shared__ double out[2];
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(256)
     const uchar4* m4 = reinterpret_cast<const uchar4*>(maskp);
     double rzd = 0.0, rrd = 0.0;
     for (long long n = gtid(); n < v4; n += gstride()) {
-        const float4 di = __ldg(di4 + n);
+        const float4 di = JB ? __ldg(di4 + n) : make_float4(0.f, 0.f, 0.f, 0.f);
         const uchar4 mk = __ldg(m4 + n);
         float4 dd[3], pp[3], qq[3], rr[3];
 #pragma unroll
@@ -222,13 +225,15 @@ __global__ void __launch_bounds__(256)
             rv.w = ((mk.w >> c) & 1) ? 0.f : fmaf(-alpha, qq[c].w, rr[c].w);
             d4[c * v4 + n] = dd[c];
             r4[c * v4 + n] = rv;
-            rz = fmaf(di.x * rv.x, rv.x, rz);
-            rz = fmaf(di.y * rv.y, rv.y, rz);
-            rz = fmaf(di.z * rv.z, rv.z, rz);
-            rz = fmaf(di.w * rv.w, rv.w, rz);
+            if (JB) {
+                rz = fmaf(di.x * rv.x, rv.x, rz);
+                rz = fmaf(di.y * rv.y, rv.y, rz);
+                rz = fmaf(di.z * rv.z, rv.z, rz);
+                rz = fmaf(di.w * rv.w, rv.w, rz);
+            }
             rs = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, fmaf(rv.w, rv.w, rs))));
         }
-        rzd += rz;
+        if (JB) rzd += rz;
         rrd += rs;
     }
     double v[2] = {rzd, rrd};
@@ -387,9 +392,12 @@ void launch_pcg32_iter(to3d_ctx* c, cudaStream_t s, int prec, int parity, cudaEv
 // d += alpha p_new, r -= alpha q, |r|^2; with jacobi_beta also r.M^-1 r and
 // beta = rz_new / rz (Jacobi PCG); without, the caller forms beta itself.
 void launch_pcg32_update_mode(to3d_ctx* c, cudaStream_t s, const float* p_new, int jacobi_beta) {
-    k_pcg32_update<<<vec_blocks(c->vol / 4), PCG_THREADS, 0, s>>>(c->vol, c->d32, c->r32, p_new,
-                                                              c->q32, c->dinv32, c->maskp, c->red,
-                                                              c->ss, jacobi_beta);
+    if (jacobi_beta)
+        k_pcg32_update<1><<<vec_blocks(c->vol / 4), PCG_THREADS, 0, s>>>(
+            c->vol, c->d32, c->r32, p_new, c->q32, c->dinv32, c->maskp, c->red, c->ss);
+    else
+        k_pcg32_update<0><<<vec_blocks(c->vol / 4), PCG_THREADS, 0, s>>>(
+            c->vol, c->d32, c->r32, p_new, c->q32, c->dinv32, c->maskp, c->red, c->ss);
     c->launches++;
 }
 
