@@ -250,9 +250,10 @@ def reference_arm(args):
 
 # ------------------------------------------------------------------ GPU arm
 # DRAM bytes (read + write) of one launch of the fused tensor-core kernel at
-# 480x160x80 from one ncu capture of the current kernel (profiles/); reported
-# only for the forms and size captured.
-TC_TRAFFIC_BYTES = {(1, 480, 160, 80): 234_799_104 + 130_163_712}
+# 480x160x80 from one ncu capture of the current kernel (profiles/), keyed by
+# (precision, preconditioner, grid); reported only for the form and size
+# captured (the z-segment length, and so the halo traffic, is tuned per form).
+TC_TRAFFIC_BYTES = {(1, "lmg", 480, 160, 80): 241_737_216 + 128_706_816}
 
 
 def max_over_ranks(x: float, device) -> float:
@@ -536,7 +537,7 @@ def ours(args):
         b = algorithmic_bytes_tc(nelx, nely, nelz)
         ach = b / (tc_avg_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": TC_TRAFFIC_BYTES.get((args.precision, nelx, nely, nelz)),
+                "traffic": TC_TRAFFIC_BYTES.get((args.precision, args.precond, nelx, nely, nelz)),
                 "kernel": "k_matvec_tc (fused direction + tensor-core K p)",
                 "launch_ms": tc_avg_ms, "algorithmic_bytes": b, "samples": tc_n,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}

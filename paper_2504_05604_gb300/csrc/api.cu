@@ -154,7 +154,7 @@ static void free_all(to3d_ctx* c) {
     destroy_mg(c);
     if (c->xphys) cudaFree(c->xphys);
     void* ptrs[] = {c->x, c->xnew, c->E, c->E32, c->ce, c->dc, c->dcf, c->Hs, c->ocq, c->oclo,
-                    c->ochi, c->passive, c->nodemask, c->dinv, c->dinv32, c->f, c->ftmp, c->u,
+                    c->ochi, c->ocs, c->passive, c->nodemask, c->dinv, c->dinv32, c->f, c->ftmp, c->u,
                     c->r, c->p, c->q, c->tmp, c->d32, c->r32, c->p32a, c->p32b, c->q32,
                     c->stage, c->red.partials, c->red.counter, c->ss, c->os, c->misc,
                     c->dev_err, c->tcB, c->maskp};
@@ -619,7 +619,7 @@ to3d_status to3d_create(const to3d_params* prm, const uint8_t* fixed, const doub
     const long long nel32 = (long long)c->pex * g.nely * g.nelz;
     AL(c->x, nel); AL(c->xnew, nel); AL(c->E, nel); AL(c->E32, nel32);
     AL(c->ce, nel); AL(c->dc, nel); AL(c->dcf, nel); AL(c->Hs, nel);
-    AL(c->ocq, nel); AL(c->oclo, nel); AL(c->ochi, nel); AL(c->passive, nel);
+    AL(c->ocq, nel); AL(c->oclo, nel); AL(c->ochi, nel); AL(c->ocs, 6 * nel); AL(c->passive, nel);
     c->px = (g.nx + 3) / 4 * 4;
     c->vol = (long long)c->px * g.ny * g.nz;
     const long long vol = c->vol;

@@ -137,30 +137,73 @@ __global__ void k_oc_init(OCScalars* os, int levels, double tol, double target, 
     oc_build_tree(os);
 }
 
+// Double-single numbers: v = hi + lo with two floats, |lo| <= ulp(hi) / 2,
+// about 48 significant bits.  The bisection passes evaluate the design
+// volume at 2^L - 1 candidates per element and pass; in FP64 that is four
+// FP64 operations per candidate and element, and this GPU's FP64 pipe is
+// narrow, so the passes work on double-single copies of q, lo and hi on the
+// FP32 pipe.  A term clamp(q t, lo, hi) is then correct to about 2^-46 of
+// its size and a pass's volume to about 1e-13 relative: a bisection decision
+// could differ from the FP64 one only if the volume at a midpoint were that
+// close to the target.
+struct DS {
+    float h, l;
+};
+__device__ __forceinline__ DS ds_from(double v) {
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ DS ds_mul(DS a, DS b) {
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);          // exact error of the leading product
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    const float s = p + e;
+    return {s, e - (s - p)};
+}
+__device__ __forceinline__ bool ds_lt(DS a, DS b) { return a.h < b.h || (a.h == b.h && a.l < b.l); }
+// acc += v (two-sum of the leading parts, the rest into the low part)
+__device__ __forceinline__ void ds_acc(DS& acc, DS v) {
+    const float s = acc.h + v.h;
+    const float bb = s - acc.h;
+    const float err = (acc.h - (s - bb)) + (v.h - bb);
+    const float l = acc.l + err + v.l;
+    const float h2 = s + l;
+    acc.l = l - (h2 - s);
+    acc.h = h2;
+}
+
 // q = x sqrt(max(0,-dcf)), lo = max(0, x-move), hi = min(1, x+move); passive
 // elements get q = lo = hi = 0 so they add nothing to the design volume.
+// FP64 for the final update, double-single copies for the passes.
 __global__ void k_oc_prep(long long nel, const double* __restrict__ x,
                           const double* __restrict__ dcf, const uint8_t* __restrict__ passive,
                           double move, double* __restrict__ q, double* __restrict__ lo,
-                          double* __restrict__ hi) {
+                          double* __restrict__ hi, float* __restrict__ qs) {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= nel) return;
     const double xe = x[e];
-    if (passive[e]) {
-        q[e] = lo[e] = hi[e] = 0.0;
-        return;
+    double qe = 0.0, le = 0.0, he = 0.0;
+    if (!passive[e]) {
+        qe = xe * sqrt(fmax(0.0, -dcf[e]));
+        le = fmax(0.0, xe - move);
+        he = fmin(1.0, xe + move);
     }
-    q[e] = xe * sqrt(fmax(0.0, -dcf[e]));
-    lo[e] = fmax(0.0, xe - move);
-    hi[e] = fmin(1.0, xe + move);
+    q[e] = qe;
+    lo[e] = le;
+    hi[e] = he;
+    const DS a = ds_from(qe), b = ds_from(le), c = ds_from(he);
+    float2* o = reinterpret_cast<float2*>(qs + 6 * e);
+    o[0] = make_float2(a.h, a.l);
+    o[1] = make_float2(b.h, b.l);
+    o[2] = make_float2(c.h, c.l);
 }
 
 // One pass: design volume at every candidate of the tree, then the last
 // block walks the tree exactly as the scalar bisection would.
 template <int LEV>
 __global__ void __launch_bounds__(EL_THREADS)
-    k_oc_pass(long long nel, const double* __restrict__ q, const double* __restrict__ lo,
-              const double* __restrict__ hi, const Reducer red, OCScalars* os,
+    k_oc_pass(long long nel, const float* __restrict__ qs, const Reducer red, OCScalars* os,
               cudaGraphConditionalHandle loop, int use_loop) {
     if (os->done) {
         // inside a graph loop the body must always decide the loop condition
@@ -170,21 +213,35 @@ __global__ void __launch_bounds__(EL_THREADS)
     constexpr int NC = (1 << LEV) - 1;
     __shared__ double sh[32 * NC];
     __shared__ double out[NC];
-    __shared__ double st[NC];
-    if (threadIdx.x < NC) st[threadIdx.x] = 1.0 / sqrt(os->cand[threadIdx.x]);
+    __shared__ float2 st[NC];
+    if (threadIdx.x < NC) {
+        // capped so that it stays finite in FP32 (q t then clamps at hi, or
+        // is 0 for q = 0, as in FP64)
+        const DS t = ds_from(fmin(1.0 / sqrt(os->cand[threadIdx.x]), 1e30));
+        st[threadIdx.x] = make_float2(t.h, t.l);
+    }
     __syncthreads();
-    double t[NC];
+    DS t[NC], acc[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) t[c] = st[c];
-    double v[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) v[c] = 0.0;
+    for (int c = 0; c < NC; ++c) {
+        t[c] = {st[c].x, st[c].y};
+        acc[c] = {0.f, 0.f};
+    }
+    const float2* q2 = reinterpret_cast<const float2*>(qs);
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nel;
          e += (long long)gridDim.x * blockDim.x) {
-        const double qe = q[e], le = lo[e], he = hi[e];
+        const float2 a = __ldg(q2 + 3 * e), b = __ldg(q2 + 3 * e + 1), d = __ldg(q2 + 3 * e + 2);
+        const DS qe{a.x, a.y}, le{b.x, b.y}, he{d.x, d.y};
 #pragma unroll
-        for (int c = 0; c < NC; ++c) v[c] += fmax(le, fmin(he, qe * t[c]));
+        for (int c = 0; c < NC; ++c) {
+            // clamp(q t, lo, hi) with lo <= hi
+            const DS v = ds_mul(qe, t[c]);
+            ds_acc(acc[c], ds_lt(v, le) ? le : (ds_lt(he, v) ? he : v));
+        }
     }
+    double v[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) v[c] = (double)acc[c].h + (double)acc[c].l;
     if (grid_sum<NC>(red, v, sh, out) && threadIdx.x == 0) {
         int node = 0;
         for (int lev = 0; lev < LEV; ++lev) {
@@ -306,7 +363,7 @@ void launch_filter(to3d_ctx* c, cudaStream_t s, int mode, const double* a, const
 void launch_oc_begin(to3d_ctx* c, cudaStream_t s, const double* x, const double* dcf,
                      double target) {
     k_oc_prep<<<el_blocks(c->g.nel), EL_THREADS, 0, s>>>(c->g.nel, x, dcf, c->passive,
-                                                        c->prm.move, c->ocq, c->oclo, c->ochi);
+                                                        c->prm.move, c->ocq, c->oclo, c->ochi, c->ocs);
     k_oc_init<<<1, 1, 0, s>>>(c->os, c->prm.oc_levels, c->prm.bisect_tol, target, 400);
     c->launches += 2;
 }
@@ -316,11 +373,11 @@ void launch_oc_passes(to3d_ctx* c, cudaStream_t s, int npass, cudaGraphCondition
     const unsigned nb = el_blocks_capped(c->g.nel);
     for (int i = 0; i < npass; ++i) {
         switch (c->prm.oc_levels) {
-            case 1: k_oc_pass<1><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocq, c->oclo, c->ochi, c->red, c->os, loop, use_loop); break;
-            case 2: k_oc_pass<2><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocq, c->oclo, c->ochi, c->red, c->os, loop, use_loop); break;
-            case 3: k_oc_pass<3><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocq, c->oclo, c->ochi, c->red, c->os, loop, use_loop); break;
-            case 4: k_oc_pass<4><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocq, c->oclo, c->ochi, c->red, c->os, loop, use_loop); break;
-            default: k_oc_pass<5><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocq, c->oclo, c->ochi, c->red, c->os, loop, use_loop); break;
+            case 1: k_oc_pass<1><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocs, c->red, c->os, loop, use_loop); break;
+            case 2: k_oc_pass<2><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocs, c->red, c->os, loop, use_loop); break;
+            case 3: k_oc_pass<3><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocs, c->red, c->os, loop, use_loop); break;
+            case 4: k_oc_pass<4><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocs, c->red, c->os, loop, use_loop); break;
+            default: k_oc_pass<5><<<nb, EL_THREADS, 0, s>>>(c->g.nel, c->ocs, c->red, c->os, loop, use_loop); break;
         }
         c->launches++;
     }
