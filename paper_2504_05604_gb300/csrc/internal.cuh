@@ -125,7 +125,6 @@ struct to3d_ctx {
     float tc_cscale = 1.f;                // scale of the combined integer B
     double tc_cscale_d = 1.0;             // the same scale in FP64
     double tc_bmax = 0.0;                 // max |B| of the combined integer B
-    double tc_browl1 = 0.0;               // max row sum of |B| of the combined integer B
     int tc_lz = 20;                       // node layers per z segment of a tile
     int tc_grid = 608;                    // persistent CTAs
     long long ndesign = 0;                // number of design (non-passive) elements

@@ -551,38 +551,50 @@ __global__ void k_pow_start(const Grid g, int px, long long vol, const float* __
 }
 
 // out[0] = z.t, out[1] = z.D z (D = 1 / dinv on dofs with dinv > 0)
-__global__ void k_pow_dots(long long vol, const float* __restrict__ z, const float* __restrict__ t,
-                           const float* __restrict__ dinv, const uint8_t* __restrict__ maskp,
-                           const Reducer red, double* out_dev) {
+// Four consecutive nodes per step (vol is a multiple of 4: 16-byte loads);
+// FP32 products and partial sums of a step (a Rayleigh quotient needs no
+// more), FP64 across steps, blocks and the grid.
+__global__ void __launch_bounds__(256)
+    k_pow_dots(long long vol, const float* __restrict__ z, const float* __restrict__ t,
+               const float* __restrict__ dinv, const uint8_t* __restrict__ maskp, const Reducer red,
+               double* out_dev) {
     __shared__ double sh[64];
     __shared__ double o2[2];
-    // FP32 products and partial sums over up to 8 nodes (a Rayleigh quotient
-    // needs no more), FP64 beyond, across blocks and the grid
+    const long long v4 = vol >> 2;
+    const float4* z4 = reinterpret_cast<const float4*>(z);
+    const float4* t4 = reinterpret_cast<const float4*>(t);
+    const float4* di4 = reinterpret_cast<const float4*>(dinv);
+    const uchar4* m4 = reinterpret_cast<const uchar4*>(maskp);
     double a = 0.0, b = 0.0;
-    float pa = 0.f, pb = 0.f;
-    int cnt = 0;
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < vol;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < v4;
          n += (long long)gridDim.x * blockDim.x) {
-        const float di = dinv[n];
-        const uint8_t m = maskp[n];
-        if (!(di > 0.f)) continue;
-        const float dn = 1.f / di;
+        const float4 di = __ldg(di4 + n);
+        const uchar4 mk = __ldg(m4 + n);
+        float4 zz[3], tt[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            if ((m >> c) & 1) continue;
-            const float zv = z[c * vol + n];
-            pa = fmaf(zv, t[c * vol + n], pa);
-            pb = fmaf(zv * zv, dn, pb);
+            zz[c] = __ldg(z4 + c * v4 + n);
+            tt[c] = __ldg(t4 + c * v4 + n);
         }
-        if (++cnt == 8) {
-            a += (double)pa;
-            b += (double)pb;
-            pa = pb = 0.f;
-            cnt = 0;
+        const float dv[4] = {di.x, di.y, di.z, di.w};
+        const uint8_t mv[4] = {mk.x, mk.y, mk.z, mk.w};
+        float pa = 0.f, pb = 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (!(dv[k] > 0.f)) continue;
+            const float dn = 1.f / dv[k];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if ((mv[k] >> c) & 1) continue;
+                const float zv = k == 0 ? zz[c].x : k == 1 ? zz[c].y : k == 2 ? zz[c].z : zz[c].w;
+                const float tv = k == 0 ? tt[c].x : k == 1 ? tt[c].y : k == 2 ? tt[c].z : tt[c].w;
+                pa = fmaf(zv, tv, pa);
+                pb = fmaf(zv * zv, dn, pb);
+            }
         }
+        a += (double)pa;
+        b += (double)pb;
     }
-    a += (double)pa;
-    b += (double)pb;
     double v[2] = {a, b};
     if (grid_sum<2>(red, v, sh, o2) && threadIdx.x == 0) {
         out_dev[0] = o2[0];
@@ -1060,7 +1072,7 @@ static void setup_levels_on(to3d_ctx* c, cudaStream_t s) {
         k_pow_start<<<nblocks(k->vol), kThreads, 0, s>>>(k->g, k->px, k->vol, k->dinv32, k->maskp, L.z);
         for (int it = 0; it < kPowerSteps; ++it) {
             launch_matvec_tc_io(k, s, m->prec, false, k->tm_r, L.tm_z, k->tm_d, nullptr, L.t, nullptr);
-            k_pow_dots<<<nblocks(k->vol), kThreads, 0, s>>>(k->vol, L.z, L.t, k->dinv32, k->maskp, k->red, out);
+            k_pow_dots<<<nblocks(k->vol / 4), 256, 0, s>>>(k->vol, L.z, L.t, k->dinv32, k->maskp, k->red, out);
             if (it + 1 < kPowerSteps)
                 k_pow_next<<<nblocks(k->vol), kThreads, 0, s>>>(k->vol, L.t, k->dinv32, k->maskp, out, L.z);
         }
