@@ -187,8 +187,9 @@ TO3D_API to3d_status to3d_get_density(to3d_ctx* ctx, double* x, int32_t on_devic
 TO3D_API to3d_status to3d_set_density(to3d_ctx* ctx, const double* x, int32_t on_device);
 TO3D_API to3d_status to3d_get_displacement(to3d_ctx* ctx, double* u, int32_t on_device);
 /* Checkpoint / resume: x (set_density; host values must lie in [0, 1], else
- * EINVAL), u (the next solve's warm start) and the OC iteration counter of
- * a context.  A context given the x, u and iteration of another one repeats
+ * EINVAL and x is left unchanged; they are checked on the GPU after the
+ * copy; device values are taken as given), u (the next solve's warm start)
+ * and the OC iteration counter of a context.  A context given the x, u and iteration of another one repeats
  * that one's next OC iteration exactly. */
 TO3D_API to3d_status to3d_set_displacement(to3d_ctx* ctx, const double* u, int32_t on_device);
 TO3D_API to3d_status to3d_get_iteration(const to3d_ctx* ctx, int32_t* iter);

@@ -722,12 +722,21 @@ to3d_status to3d_get_density(to3d_ctx* c, double* x, int32_t on_device) {
 to3d_status to3d_set_density(to3d_ctx* c, const double* x, int32_t on_device) {
     if (!c || !x) return TO3D_EINVAL;
     const size_t b = c->g.nel * sizeof(double);
-    if (!on_device)
-        for (long long e = 0; e < c->g.nel; ++e)
-            if (!(x[e] >= 0.0 && x[e] <= 1.0)) return set_err(c, TO3D_EINVAL, "densities must lie in [0, 1]");
-    CK(cudaMemcpyAsync(c->x, x, b, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                       c->stream));
-    if (!on_device) CK(cudaStreamSynchronize(c->stream));
+    if (on_device) {
+        CK(cudaMemcpyAsync(c->x, x, b, cudaMemcpyDeviceToDevice, c->stream));
+        return TO3D_OK;
+    }
+    // host input: staged in the OC output buffer (free between iterations)
+    // and range-checked there on the GPU, so a rejected design leaves x as it was
+    int* bad = reinterpret_cast<int*>(c->misc + 7);
+    int bad_h = 0;
+    CK(cudaMemcpyAsync(c->xnew, x, b, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+    launch_check_unit(c, c->stream, c->xnew, bad);
+    CK(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (bad_h) return set_err(c, TO3D_EINVAL, "densities must lie in [0, 1]");
+    CK(cudaMemcpyAsync(c->x, c->xnew, b, cudaMemcpyDeviceToDevice, c->stream));
     return TO3D_OK;
 }
 

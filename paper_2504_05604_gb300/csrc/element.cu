@@ -301,6 +301,15 @@ __global__ void __launch_bounds__(EL_THREADS)
     }
 }
 
+// ---------------------------------------------------------------- input check
+// *bad = 1 if any x_e lies outside [0, 1] (or is NaN); the flag is cleared
+// by the caller
+__global__ void k_check_unit(long long n, const double* __restrict__ x, int* bad) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x)
+        if (!(x[e] >= 0.0 && x[e] <= 1.0)) *bad = 1;
+}
+
 // ---------------------------------------------------------------- launchers
 static unsigned el_blocks(long long n) { return (unsigned)((n + EL_THREADS - 1) / EL_THREADS); }
 static unsigned el_blocks_capped(long long n) {
@@ -332,6 +341,11 @@ __global__ void k_pin_passive(long long nel, const uint8_t* __restrict__ passive
     const uint8_t t = passive[e];
     if (t == 1) x[e] = void_val;
     else if (t == 2) x[e] = solid_val;
+}
+
+void launch_check_unit(to3d_ctx* c, cudaStream_t s, const double* x, int* bad) {
+    k_check_unit<<<el_blocks_capped(c->g.nel), EL_THREADS, 0, s>>>(c->g.nel, x, bad);
+    c->launches++;
 }
 
 void launch_pin_passive(to3d_ctx* c, cudaStream_t s, double* x) {

@@ -213,6 +213,7 @@ void init_tc_attributes();
 bool prepare_tc_operands(to3d_ctx* c);
 
 // element.cu
+void launch_check_unit(to3d_ctx* c, cudaStream_t s, const double* x, int* bad);
 void launch_pin_passive(to3d_ctx* c, cudaStream_t s, double* x);
 void launch_zero_passive(to3d_ctx* c, cudaStream_t s, double* v);
 void launch_sensitivity(to3d_ctx* c, cudaStream_t s, const double* x, const double* u,

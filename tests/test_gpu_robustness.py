@@ -30,11 +30,17 @@ def test_set_density_refuses_bad_values():
     from paper_2504_05604_gb300 import To3dError
     prob = problems.cantilever(6, 3, 2)
     ctx = lib_ctx(prob)
+    x0 = ctx.density()
     for bad in (np.nan, -0.1, 1.5):
         x = np.full(prob.nel, 0.3)
         x[2] = bad
         with pytest.raises(To3dError):
             ctx.set_density(x)
+        # a refused design leaves the context's design as it was
+        assert np.array_equal(ctx.density(), x0)
+    x = np.linspace(0.0, 1.0, prob.nel)
+    ctx.set_density(x)
+    assert np.array_equal(ctx.density(), x)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
