@@ -47,14 +47,20 @@ def test_stored_volumes_on_target():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", [0, 1, 2, 3])
-def test_gpu_loop_matches_stored_trajectory(precision):
+@pytest.mark.parametrize("precision,lmg", [(0, False), (1, False), (2, False), (3, False), (1, True)])
+def test_gpu_loop_matches_stored_trajectory(precision, lmg):
+    """Every precision with Jacobi, and the benchmark's form (BF16 defect
+    correction, learned multigrid with its default parameters, kept inner
+    direction, inner tolerance 0.05, FP64 residuals on the sliced
+    tensor-core K u)."""
     import __graft_entry__ as ge
     ge.build()
     from tests.gpu_helpers import lib_ctx
+    from paper_2504_05604_gb300 import LMG
     g = golden()
     prob = problem(g)
-    ctx = lib_ctx(prob, precision=precision)
+    kw = dict(precond=LMG, inner_rtol=0.05, mg_keep_dir=1, fp64_tc=1) if lmg else {}
+    ctx = lib_ctx(prob, precision=precision, **kw)
     recs = ctx.run(g["problem"]["iters"])
     comp = np.array([r["compliance"] for r in recs])
     vol = np.array([r["volume"] for r in recs])

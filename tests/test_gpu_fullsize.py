@@ -59,14 +59,22 @@ def test_full_size_matvecs_on_sampled_rows(big):
     ctx.close()
 
 
-def test_full_size_oc_iteration_properties(big):
-    """One OC iteration of the benchmark's form from x0: true FP64 residual at
-    most 1e-8 (the library's own and the oracle's recomputation), volume on target to the bisection tolerance, the energy
-    identity f^T u = sum E_e ce_e, and ce_e = u_e^T KE u_e on sampled
-    elements of the library's own displacement."""
-    from paper_2504_05604_gb300 import BF16_DC
+@pytest.mark.parametrize("form", ["jacobi", "lmg"])
+def test_full_size_oc_iteration_properties(big, form):
+    """One OC iteration from x0 in the BF16 defect-correction form with the
+    Jacobi preconditioner and in the benchmark's form (learned multigrid,
+    kept inner direction, inner tolerance 0.05, FP64 residuals on the sliced
+    tensor-core K u): true FP64 residual at most 1e-8 (the library's own and
+    the oracle's recomputation), volume on target to the bisection
+    tolerance, the energy identity f^T u = sum E_e ce_e, and
+    ce_e = u_e^T KE u_e on sampled elements of the library's own
+    displacement."""
+    from paper_2504_05604_gb300 import BF16_DC, LMG
     prob = big
-    ctx = lib_ctx(prob, precision=BF16_DC)
+    if form == "lmg":
+        ctx = lib_ctx(prob, precision=BF16_DC, precond=LMG, inner_rtol=0.05, mg_keep_dir=1, fp64_tc=1)
+    else:
+        ctx = lib_ctx(prob, precision=BF16_DC)
     rec = ctx.step()
     assert rec["status"] == 0 and rec["relres"] <= 1e-8
     assert abs(rec["volume"] / prob.volfrac - 1.0) <= 1e-3

@@ -117,13 +117,16 @@ def test_solve_with_multigrid_matches_direct(prec, tol):
     jac.close()
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_oc_trajectory_with_multigrid_matches_oracle(prec):
+@pytest.mark.parametrize("prec,kw", [(0, {}), (1, {}),
+                                     (1, dict(inner_rtol=0.05, mg_keep_dir=1, fp64_tc=1))])
+def test_oc_trajectory_with_multigrid_matches_oracle(prec, kw):
+    """The last case is the benchmark's form: kept inner direction, inner
+    tolerance 0.05, FP64 residuals on the sliced tensor-core K u."""
     from paper_2504_05604_gb300 import LMG
     prob = problems.cantilever(30, 10, 4, load="edge", volfrac=0.3, rmin=1.5)
     iters = 6
     x_ref, hist = topopt.top3d(prob, iters=iters, solver="direct")
-    ctx = lib_ctx(prob, precision=prec, precond=LMG, inner_rtol=0.01)
+    ctx = lib_ctx(prob, precision=prec, precond=LMG, **{"inner_rtol": 0.01, **kw})
     recs = ctx.run(iters)
     for r, h in zip(recs, hist):
         assert r["status"] == 0 and r["relres"] <= 1e-8
