@@ -1,6 +1,6 @@
-"""FP64-accurate K p on the tensor cores by exact integer slicing (SURVEY
-NEXT-2) against the oracle's assembled FP64 operator, the CUDA-core FP64
-kernel, and in whole solves."""
+"""FP64-accurate K p on the tensor cores by exact integer slicing (the
+operator of Section 2.2) against the oracle's assembled FP64 operator, the
+CUDA-core FP64 kernel, and in whole solves."""
 import numpy as np
 import pytest
 
