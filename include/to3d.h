@@ -103,11 +103,12 @@ typedef struct {
     int32_t mg_sweeps;   /* TO3D_LMG: Jacobi sweeps on the coarsest level
                           * (0: 6)                                            */
     int32_t fp64_tc;     /* 1: every FP64 K p (the FP64 forms' matvec, the
-                          * defect correction's residual, flexible CG) on the
-                          * tensor cores by exact integer slicing of p (FP64
-                          * accuracy; needs a nu whose lambda / mu is a small
-                          * rational, else the CUDA-core FP64 kernel runs);
-                          * 0 (default): the CUDA-core FP64 kernel            */
+                          * defect correction's residual, flexible CG) and
+                          * the element energies u_e^T KE u_e on the tensor
+                          * cores by exact integer slicing (FP64 accuracy;
+                          * needs a nu whose lambda / mu is a small rational,
+                          * else the CUDA-core FP64 kernels run);
+                          * 0 (default): the CUDA-core FP64 kernels           */
     int32_t mg_keep_dir; /* TO3D_LMG with a *_DC precision: 1 keeps the inner
                           * CG's direction across FP64 residual replacements
                           * (Fletcher-Reeves beta right after one), 0 restarts
@@ -218,7 +219,9 @@ TO3D_API to3d_status to3d_solve(to3d_ctx* ctx, const double* x, const double* f,
                        int32_t on_device, to3d_solve_info* info);
 
 /* ce_e = u_e^T KE u_e, dc_e = -p x_e^(p-1) (E0 - Emin) ce_e and
- * c = sum_e E_e ce_e (Section 2.3).  ce, dc [nel]; *compliance on host. */
+ * c = sum_e E_e ce_e (Section 2.3).  ce, dc [nel]; *compliance on host.
+ * With params.fp64_tc the energies come from the sliced tensor-core path
+ * (the element's exact products B V dotted with u_e in FP64). */
 TO3D_API to3d_status to3d_sensitivity(to3d_ctx* ctx, const double* x, const double* u, double* ce,
                              double* dc, double* compliance, int32_t on_device);
 

@@ -47,6 +47,27 @@ __global__ void __launch_bounds__(EL_THREADS)
     if (grid_sum<1>(red, v, sh, out) && threadIdx.x == 0) *comp_out = out[0];
 }
 
+// dc_e = -p x^(p-1) (E0-Emin) ce_e and c = sum E_e ce_e from energies
+// computed elsewhere (the sliced tensor-core path), same formulas as above.
+__global__ void __launch_bounds__(EL_THREADS)
+    k_sens_from_ce(long long nel, const double* __restrict__ x, const double* __restrict__ ce,
+                   double penal, double E0, double Emin, double* __restrict__ dc_out,
+                   const Reducer red, double* comp_out) {
+    __shared__ double sh[32];
+    __shared__ double out[1];
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double contrib = 0.0;
+    if (e < nel) {
+        const double xe = x[e], c = ce[e];
+        const double xp1 = (penal == 3.0) ? xe * xe : pow(xe, penal - 1.0);
+        const double Ee = Emin + xp1 * xe * (E0 - Emin);
+        dc_out[e] = -penal * xp1 * (E0 - Emin) * c;
+        contrib = Ee * c;
+    }
+    double v[1] = {contrib};
+    if (grid_sum<1>(red, v, sh, out) && threadIdx.x == 0) *comp_out = out[0];
+}
+
 // ---------------------------------------------------------------- filter
 __device__ __forceinline__ void unpack_off(int o, int& di, int& dj, int& dk) {
     di = (o & 0xff) - 16;
@@ -320,6 +341,14 @@ static unsigned el_blocks_capped(long long n) {
 
 void launch_sensitivity(to3d_ctx* c, cudaStream_t s, const double* x, const double* u,
                         double* ce, double* dc) {
+    if (c->prm.fp64_tc && matvec_x64_available(c)) {
+        // energies on the tensor cores by exact slicing, then dc and c
+        launch_energies_x64(c, s, u, ce);
+        k_sens_from_ce<<<el_blocks(c->g.nel), EL_THREADS, 0, s>>>(
+            c->g.nel, x, ce, c->prm.penal, c->prm.E0, c->prm.Emin, dc, c->red, c->misc + 0);
+        c->launches++;
+        return;
+    }
     k_sensitivity<<<el_blocks(c->g.nel), EL_THREADS, 0, s>>>(
         c->ke, c->g, x, u, c->prm.penal, c->prm.E0, c->prm.Emin, ce, dc, c->red, c->misc + 0);
     c->launches++;

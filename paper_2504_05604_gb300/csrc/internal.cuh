@@ -199,6 +199,8 @@ void launch_matvec_tc(to3d_ctx* c, cudaStream_t s, int prec, bool fused, int par
 bool matvec_x64_available(const to3d_ctx* c);
 void launch_matvec_x64(to3d_ctx* c, cudaStream_t s, const double* E, const double* p, double* y,
                        bool dot_pq);
+// element energies ce_e = u_e^T KE u_e by the same slicing (needs matvec_x64_available)
+void launch_energies_x64(to3d_ctx* c, cudaStream_t s, const double* u, double* ce);
 void launch_matvec_tc_io(to3d_ctx* c, cudaStream_t s, int prec, bool fused, const CUtensorMap& tr,
                          const CUtensorMap& tp, const CUtensorMap& td, float* p_new, float* q,
                          SolverScalars* ss);

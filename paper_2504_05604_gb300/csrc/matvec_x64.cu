@@ -71,6 +71,7 @@ struct X64Args {
     Reducer red;
     SolverScalars* ss;
     int dot_pq;
+    double* ce;                 // energy mode (non-null): ce_e = u_e^T KE u_e per element, no y
     int* err;
 };
 
@@ -115,8 +116,8 @@ __global__ void __launch_bounds__(X64_THREADS, 2) k_matvec_x64(const __grid_cons
     tc::tc_fence_after();
     const uint32_t tmem = *s_taddr;
 
-    // node plane gz of p into ring slot `slot` (clamped dofs and nodes
-    // outside the grid as 0)
+    // node plane gz of p into ring slot `slot` (nodes outside the grid as 0,
+    // and clamped dofs too unless in energy mode)
     auto load_plane = [&](int gz, int slot) {
         double* dst = sP + slot * X64_PLANE;
         for (int idx = tid; idx < X64_PLANE; idx += X64_THREADS) {
@@ -125,7 +126,8 @@ __global__ void __launch_bounds__(X64_THREADS, 2) k_matvec_x64(const __grid_cons
             double v = 0.0;
             if (gi >= 0 && gi < g.nx && gj >= 0 && gj < g.ny && gz >= 0 && gz < g.nz) {
                 const long long nd = node_id(g, gi, gj, gz);
-                if (!((a.nodemask[nd] >> c) & 1)) v = a.p[3 * nd + c];
+                // energies take u as given; K p treats clamped dofs as 0
+                if (a.ce || !((a.nodemask[nd] >> c) & 1)) v = a.p[3 * nd + c];
             }
             dst[idx] = v;
         }
@@ -216,7 +218,9 @@ __global__ void __launch_bounds__(X64_THREADS, 2) k_matvec_x64(const __grid_cons
         // ---- recombine the slices exactly and scale; the lower-half corners
         // (c = 0) plus the carried upper halves of the element below in this
         // column give this column's part of node plane kk
-        const double Ee = valid ? a.E[elem_id(g, gi, gj, kk)] : 0.0;
+        const bool energy = a.ce != nullptr;
+        const double Ee = energy ? 1.0 : (valid ? a.E[elem_id(g, gi, gj, kk)] : 0.0);
+        double ce = 0.0;
         // an Inf or NaN entry (biased exponent 2047) makes the element's
         // outputs NaN, as the FP64 kernel would
         const double scl = emax == 2047 ? __longlong_as_double(0x7FF8000000000000ll)
@@ -235,7 +239,12 @@ __global__ void __launch_bounds__(X64_THREADS, 2) k_matvec_x64(const __grid_cons
 #pragma unroll
                 for (int i = 0; i < 12; ++i) Y[i] = Y[i] * 2048 + (long long)__float2int_rn(d0[half ? i + 4 : i]);
             }
-            if (half == 0) {
+            if (energy) {
+                // u_e^T (KE u_e): the element's own entries times its outputs
+#pragma unroll
+                for (int i = 0; i < 12; ++i)
+                    ce = fma(__longlong_as_double((long long)entry(12 * half + i)), __ll2double_rn(Y[i]) * scl, ce);
+            } else if (half == 0) {
 #pragma unroll
                 for (int i = 0; i < 12; ++i) yrow[i] = fma(__ll2double_rn(Y[i]), scl, carry[i]);
             } else {
@@ -243,10 +252,13 @@ __global__ void __launch_bounds__(X64_THREADS, 2) k_matvec_x64(const __grid_cons
                 for (int i = 0; i < 12; ++i) carry[i] = __ll2double_rn(Y[i]) * scl;
             }
         }
+        // every element is owned by exactly one tile: the one whose element
+        // column, row and layer it is past the halo (ei, ej >= 1, kk >= k0)
+        if (energy && valid && ei >= 1 && ej >= 1 && kk >= k0) a.ce[elem_id(g, gi, gj, kk)] = ce;
         tc::tc_fence_before();
         __syncthreads();
         // ---- owned nodes of plane kk: the four element columns around them
-        if (kk >= k0 && tid < X64_BX * X64_BY) {
+        if (!energy && kk >= k0 && tid < X64_BX * X64_BY) {
             const int ni = 1 + tid % X64_BX, nj = 1 + tid / X64_BX;
             const int gni = i0 - 1 + ni, gnj = j0 - 1 + nj;
             if (gni < g.nx && gnj < g.ny) {
@@ -344,6 +356,40 @@ void launch_matvec_x64(to3d_ctx* c, cudaStream_t s, const double* E, const doubl
     a.red = c->red;
     a.ss = c->ss;
     a.dot_pq = dot_pq ? 1 : 0;
+    a.ce = nullptr;
+    a.err = c->dev_err;
+    const int ntiles = a.ntx * a.nty * a.ntz;
+    k_matvec_x64<<<ntiles, X64_THREADS, X64Smem::BYTES, s>>>(a);
+    c->launches++;
+}
+
+// Element energies ce_e = u_e^T KE u_e (unit modulus) by the same exact
+// slicing: the element's products B V recombined and scaled as for K u,
+// dotted with the element's own FP64 entries (24 FP64 FMAs instead of 300).
+void launch_energies_x64(to3d_ctx* c, cudaStream_t s, const double* u, double* ce) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_matvec_x64, cudaFuncAttributeMaxDynamicSharedMemorySize, X64Smem::BYTES);
+        attr = true;
+    }
+    const Grid& g = c->g;
+    X64Args a;
+    a.g = g;
+    const int nseg = (g.nz + 19) / 20;
+    a.lz = (g.nz + nseg - 1) / nseg;
+    a.ntx = (g.nx + X64_BX - 1) / X64_BX;
+    a.nty = (g.ny + X64_BY - 1) / X64_BY;
+    a.ntz = (g.nz + a.lz - 1) / a.lz;
+    a.cscale = c->tc_cscale_d;
+    a.Bimg = c->tcB + 32 * 64;
+    a.E = nullptr;
+    a.p = u;
+    a.nodemask = c->nodemask;
+    a.y = nullptr;
+    a.red = c->red;
+    a.ss = c->ss;
+    a.dot_pq = 0;
+    a.ce = ce;
     a.err = c->dev_err;
     const int ntiles = a.ntx * a.nty * a.ntz;
     k_matvec_x64<<<ntiles, X64_THREADS, X64Smem::BYTES, s>>>(a);

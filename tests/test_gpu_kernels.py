@@ -102,15 +102,18 @@ def test_solve_matches_direct(precision):
     assert np.abs(u - u_ref).max() <= tol * np.abs(u_ref).max()
 
 
+@pytest.mark.parametrize("fp64_tc", [0, 1])
 @pytest.mark.parametrize("dims", SIZES)
-def test_sensitivity(dims):
+def test_sensitivity(dims, fp64_tc):
+    """FP64 CUDA-core energies, and (fp64_tc) energies on the tensor cores by
+    exact slicing of u_e."""
     prob = random_problem(*dims, seed=21 + sum(dims))
     x = problems.random_density(prob.nel, 22, 0.0, 1.0)
     u = problems.random_vector(prob.ndof, 23)
     KE = fem.element_stiffness(prob.nu)
     ce_ref = fem.element_energies(prob.nelx, prob.nely, prob.nelz, KE, u)
     c_ref, dc_ref = fem.compliance_and_sensitivity(x, ce_ref, prob.penal)
-    ctx = lib_ctx(prob)
+    ctx = lib_ctx(prob, fp64_tc=fp64_tc)
     ce, dc, c = ctx.sensitivity(x, u)
     assert np.allclose(ce, ce_ref, rtol=1e-12, atol=1e-12 * np.abs(ce_ref).max())
     assert np.allclose(dc, dc_ref, rtol=1e-12, atol=1e-12 * np.abs(dc_ref).max())
