@@ -71,10 +71,13 @@ struct X64Args {
     Reducer red;
     SolverScalars* ss;
     int dot_pq;
-    double* ce;                 // energy mode (non-null): ce_e = u_e^T KE u_e per element, no y
+    double* ce;                 // energy form: ce_e = u_e^T KE u_e per element, no y
     int* err;
 };
 
+// ENERGY: element energies into a.ce instead of K p into a.y (a separate
+// instantiation, so the K p form carries none of its code)
+template <bool ENERGY>
 __global__ void __launch_bounds__(X64_THREADS, 2) k_matvec_x64(const __grid_constant__ X64Args a) {
     if (a.dot_pq && a.ss->done) return;
     extern __shared__ uint8_t smem_raw[];
@@ -127,7 +130,7 @@ __global__ void __launch_bounds__(X64_THREADS, 2) k_matvec_x64(const __grid_cons
             if (gi >= 0 && gi < g.nx && gj >= 0 && gj < g.ny && gz >= 0 && gz < g.nz) {
                 const long long nd = node_id(g, gi, gj, gz);
                 // energies take u as given; K p treats clamped dofs as 0
-                if (a.ce || !((a.nodemask[nd] >> c) & 1)) v = a.p[3 * nd + c];
+                if (ENERGY || !((a.nodemask[nd] >> c) & 1)) v = a.p[3 * nd + c];
             }
             dst[idx] = v;
         }
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(X64_THREADS, 2) k_matvec_x64(const __grid_cons
         // ---- recombine the slices exactly and scale; the lower-half corners
         // (c = 0) plus the carried upper halves of the element below in this
         // column give this column's part of node plane kk
-        const bool energy = a.ce != nullptr;
+        constexpr bool energy = ENERGY;
         const double Ee = energy ? 1.0 : (valid ? a.E[elem_id(g, gi, gj, kk)] : 0.0);
         double ce = 0.0;
         // an Inf or NaN entry (biased exponent 2047) makes the element's
@@ -336,7 +339,7 @@ void launch_matvec_x64(to3d_ctx* c, cudaStream_t s, const double* E, const doubl
                        bool dot_pq) {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_matvec_x64, cudaFuncAttributeMaxDynamicSharedMemorySize, X64Smem::BYTES);
+        cudaFuncSetAttribute(k_matvec_x64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, X64Smem::BYTES);
         attr = true;
     }
     const Grid& g = c->g;
@@ -359,7 +362,7 @@ void launch_matvec_x64(to3d_ctx* c, cudaStream_t s, const double* E, const doubl
     a.ce = nullptr;
     a.err = c->dev_err;
     const int ntiles = a.ntx * a.nty * a.ntz;
-    k_matvec_x64<<<ntiles, X64_THREADS, X64Smem::BYTES, s>>>(a);
+    k_matvec_x64<false><<<ntiles, X64_THREADS, X64Smem::BYTES, s>>>(a);
     c->launches++;
 }
 
@@ -369,7 +372,7 @@ void launch_matvec_x64(to3d_ctx* c, cudaStream_t s, const double* E, const doubl
 void launch_energies_x64(to3d_ctx* c, cudaStream_t s, const double* u, double* ce) {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_matvec_x64, cudaFuncAttributeMaxDynamicSharedMemorySize, X64Smem::BYTES);
+        cudaFuncSetAttribute(k_matvec_x64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, X64Smem::BYTES);
         attr = true;
     }
     const Grid& g = c->g;
@@ -392,7 +395,7 @@ void launch_energies_x64(to3d_ctx* c, cudaStream_t s, const double* u, double* c
     a.ce = ce;
     a.err = c->dev_err;
     const int ntiles = a.ntx * a.nty * a.ntz;
-    k_matvec_x64<<<ntiles, X64_THREADS, X64Smem::BYTES, s>>>(a);
+    k_matvec_x64<true><<<ntiles, X64_THREADS, X64Smem::BYTES, s>>>(a);
     c->launches++;
 }
 
