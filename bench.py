@@ -196,7 +196,9 @@ def cpu_leg(args):
                        f"iterations timed ({t_it:.3f} s each at full size), CSR assembly "
                        f"({t_asm:.2f} s) and energies + filter + OC ({t_el:.2f} s), each scaled by "
                        f"element count; OC iteration = {args.cpu_its:.0f} PCG iterations (the "
-                       f"library's FP64 Jacobi-PCG count on the same designs) + the rest"),
+                       f"library's FP64 Jacobi-PCG count on the bench designs, "
+                       f"{'measured in this run' if args.cpu_its != REF_ITERS_PER_OC else 'its mean over OC iterations 4-11 at this size from earlier runs'}"
+                       f") + the rest"),
             "t_pcg_iter_s": t_it, "t_assembly_s": t_asm, "t_elementwise_s": t_el,
             "pcg_iters_per_oc": args.cpu_its, "nproc": os.cpu_count()}
 
